@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Throughput of the segmentation chain on 4096 x 4096 nuclei tiles.
+
+One step = the whole chain (marker, reconstruction by dilation, threshold,
+hole filling, labeling with the area filter, squared EDT) over one batch of
+synthetic 4096 x 4096 tiles already resident in HBM. The metric is 4K x 4K
+tiles per second (outputs bit-exact with the CPU oracle, checked by the
+tests). Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl native|reference]
+
+--impl reference times the CPU oracle (the plain C implementation the tests
+check against) on the host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "4Kx4K tiles/s (bit-exact segmentation chain)"
+UNIT = "tiles/s"
+BYTES_CHAIN = 9          # compulsory bytes/px: input 1 + labels 4 + EDT 4
+BYTES_RF = 2             # R and F outputs, 1 byte each
+BYTES_RECON = 2          # reconstruction: read mask 1, write R 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=8, help="tiles per step per GPU")
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    return ap.parse_args()
+
+
+def _gen(args):
+    seed, size = args
+    import synth
+    return synth.config2_tile(seed, H=size, W=size)
+
+
+def make_tiles(n, rank, size):
+    """Seeded 4K nuclei tiles, generated in a spawn pool before any CUDA call."""
+    import multiprocessing as mp
+    seeds = [(2000 + 100 * rank + i, size) for i in range(n)]
+    workers = max(1, min(n, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_gen, seeds)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        mhz, maxes, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(maxes), "samples": len(mhz),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_tiles_per_s(tiles, threads):
+    """Oracle chain over `tiles`, one tile per host thread (the C oracle
+    releases the GIL). Returns (tiles/s, seconds)."""
+    import concurrent.futures as cf
+
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(oracle.chain, tiles))
+    dt = time.perf_counter() - t0
+    return len(tiles) / dt, dt
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    tiles = make_tiles(a.batch, 0, a.size)
+    threads = min(os.cpu_count() or 1, a.batch)
+    for _ in range(a.warmup):
+        oracle_tiles_per_s(tiles, threads)
+    times = []
+    for _ in range(a.steps):
+        _, dt = oracle_tiles_per_s(tiles, threads)
+        times.append(dt)
+    total = sum(times)
+    value = a.batch * a.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * total / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32",
+        "data": "synthetic",
+        "config": {"workload": f"segmentation chain, {a.batch} x {a.size}x{a.size} nuclei tiles per step",
+                   "tiles_per_step": a.batch, "side": a.size},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{a.batch} tiles of {a.size}x{a.size} per step, one tile per host thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- native
+def run_native(a, rank, world, local_rank):
+    tiles = make_tiles(a.batch, rank, a.size)     # before the first CUDA call
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1405_7958_gb300 as rt
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx = rt.Context(local_rank)
+    params = rt.SegParams()
+    stream = torch.cuda.current_stream()
+    imgs = [torch.from_numpy(t).to(dev) for t in tiles]
+    outs = None
+    for _ in range(a.warmup):
+        outs = rt.segment_batch(imgs, params, outputs=outs, ctx=ctx)
+    torch.cuda.synchronize()
+    rounds = ctx.last_rounds()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    ctx.timing(True)
+    ctx.read_timing(reset=True)
+    l0 = ctx.kernel_launches()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    barrier()
+    for k in range(a.steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record(stream)
+        outs = rt.segment_batch(imgs, params, outputs=outs, ctx=ctx)
+        evs[k][1].record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = ctx.kernel_launches() - l0
+    step_ms = [s.elapsed_time(e) for s, e in evs]
+    phases = ctx.read_timing(reset=True)
+    ctx.timing(False)
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    px = a.size * a.size
+    value = world * a.batch * a.steps / (total_ms / 1000.0)
+
+    # dominant kernel: the propagation sweeps (one launch per step)
+    sweep_ms, sweep_n = phases["recon_sweep"]
+    peak, peak_kind = load_peaks()
+    roof = None
+    if sweep_n:
+        per_launch_s = sweep_ms / sweep_n / 1000.0
+        algo_bytes = BYTES_RECON * px * a.batch
+        ach = algo_bytes / per_launch_s / 1e9
+        roof = {"kernel": "recon_sweep_kernel", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": per_launch_s * 1000}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        h_in = [torch.from_numpy(t).pin_memory() for t in tiles]
+        h_L = [torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in tiles]
+        h_D = [torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in tiles]
+        d_in = [torch.empty_like(x, device=dev) for x in imgs]
+        outs_e = None
+
+        def e2e_step():
+            nonlocal outs_e
+            for h, d in zip(h_in, d_in):
+                d.copy_(h, non_blocking=True)
+            outs_e = rt.segment_batch(d_in, params, outputs=outs_e, ctx=ctx, want_recon=False, want_filled=False)
+            for o, hl, hd in zip(outs_e, h_L, h_D):
+                hl.copy_(o["L"], non_blocking=True)
+                hd.copy_(o["D"], non_blocking=True)
+
+        for _ in range(max(1, a.warmup)):
+            e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        tt = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        # the read-back matches the device result
+        assert np.array_equal(h_L[0].numpy(), outs_e[0]["L"].cpu().numpy())
+        e2e = {"value": world * a.batch * a.steps / (float(tt.item()) / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": a.batch * px, "d2h_bytes_per_step": a.batch * px * 8}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu:
+        threads = min(os.cpu_count() or 1, a.batch)
+        v, dt = oracle_tiles_per_s(tiles, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"the {a.batch} bench tiles ({a.size}x{a.size}), one per host thread, {dt:.1f} s"}
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        chain_bytes = (BYTES_CHAIN + BYTES_RF) * px * a.batch * a.steps * world
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32", "data": "synthetic",
+            "config": {"workload": f"segmentation chain, {a.batch} x {a.size}x{a.size} nuclei tiles per step per GPU",
+                       "tiles_per_step": a.batch, "side": a.size, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MB write)"},
+            "chain_hbm_gbs": chain_bytes / (total_ms / 1000.0) / 1e9,
+            "roofline": roof,
+            "phases_ms_per_step": {k: v[0] / a.steps for k, v in phases.items()},
+            "recon_rounds_last_tile_batch": rounds,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "step_ms": [round(x, 4) for x in step_ms],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_native(a, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * rt.h -- C ABI of the GB300 (sm_103a) segmentation hot path.
+ *
+ * The operations are the per-tile segmentation functions of the microscopy
+ * pipeline in Teodoro et al., "Region Templates: Data Representation and
+ * Management for Large-Scale Image Analysis": ReconToNuclei, FillHoles,
+ * Pre-Watershed and BWLabel (Section 5.1, "Example Application") and
+ * AreaThreshold (Section 3.2.1, "PATS"). The paper states that a
+ * segmentation stage takes an image tile and produces a mask array
+ * (Section 4, "Global Storage Implementations for Data Regions"). It names
+ * the functions but does not define them; each entry point below states the
+ * textbook definition it computes, and all results are unique, so every
+ * variant returns identical bytes.
+ *
+ * Conventions for every entry point:
+ *  - Image pointers are DEVICE pointers owned by the caller; the library
+ *    never frees or retains them. Images are row-major; `ld_*` is the row
+ *    stride in ELEMENTS (bytes for uint8 images, int32 elements for int32
+ *    images) and must be >= W.
+ *  - 1 <= H, W <= 32768. conn is 4 or 8 (neighbourhood of a pixel: its 4
+ *    edge neighbours, or those plus the 4 diagonal ones). Out-of-image
+ *    neighbours do not exist.
+ *  - Binary inputs: any nonzero byte is foreground. Binary outputs are 0/1.
+ *  - All work is enqueued asynchronously on `stream` (a cudaStream_t; NULL
+ *    means the legacy default stream). Inputs must stay valid and unchanged
+ *    until the work completes.
+ *  - The return value reports synchronous failures only: invalid arguments
+ *    (RT_EINVAL), workspace allocation failure (RT_ENOMEM) or a launch error
+ *    (RT_ECUDA). Outcomes known only on the device (an iteration bound hit,
+ *    a marker above the mask) are written to `dev_status`, a device int32
+ *    the caller may pass (NULL = not reported) and read after synchronising;
+ *    it holds RT_OK or the first error code raised.
+ *  - A context owns its workspace (device scratch), grows it on demand with
+ *    cudaMalloc (which synchronises the device) and reuses it across calls.
+ *    Calls on one context must be serialised by the caller (one stream at a
+ *    time); use one context per concurrent stream.
+ */
+#ifndef RT_SEG_H
+#define RT_SEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RT_API __attribute__((visibility("default")))
+#else
+#define RT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RT_OK = 0,
+    RT_EINVAL = 1,    /* bad argument (null pointer, size, stride, conn, alias) */
+    RT_ENOMEM = 2,    /* workspace allocation failed */
+    RT_ECUDA = 3,     /* CUDA runtime error at launch */
+    RT_ETIMEOUT = 4,  /* device-side iteration or wait bound reached */
+    RT_EMARKER = 5,   /* marker above the mask somewhere (output still defined) */
+    RT_EQUEUE = 6,    /* frontier queue overflow that the fall-back could not absorb */
+    RT_EUNAVAIL = 7   /* requested variant or feature not available */
+} rt_status;
+
+/* Propagation variants of rt_reconstruct; all give identical output. */
+enum {
+    RT_AUTO = 0,    /* library choice */
+    RT_RASTER = 1,  /* tile-resident directional sweeps, active-tile rounds */
+    RT_QUEUE = 2,   /* pixel frontier queue (irregular wavefront propagation) */
+    RT_HYBRID = 3   /* sweeps while the frontier is large, then the queue */
+};
+
+typedef struct rt_ctx rt_ctx;
+
+/* Create a context bound to CUDA device `device`. Returns RT_OK and sets
+ * *ctx, or an error (the device is not usable, allocation failed). */
+RT_API rt_status rt_create(rt_ctx **ctx, int device);
+
+/* Free a context and its workspace. Waits for the device first. NULL is a
+ * no-op. */
+RT_API void rt_destroy(rt_ctx *ctx);
+
+/* Static, human-readable name of a status code. */
+RT_API const char *rt_status_str(int status);
+
+/* ABI version (major * 100 + minor). */
+RT_API int rt_version(void);
+
+/* Bytes of device workspace the context currently holds. */
+RT_API size_t rt_workspace_bytes(const rt_ctx *ctx);
+
+/*
+ * Marker of the ReconToNuclei step for nuclei tiles:
+ *     J = max(I - h_offset, 0) inside the tile, J = I on the one-pixel border.
+ * mask: uint8 H x W (ld_mask); marker: uint8 H x W output (ld_marker).
+ * 0 <= h_offset <= 255. The two buffers may not overlap.
+ */
+RT_API rt_status rt_marker(rt_ctx *ctx, const uint8_t *mask, int64_t ld_mask,
+                    uint8_t *marker, int64_t ld_marker, int H, int W, int h_offset,
+                    void *stream);
+
+/*
+ * ReconToNuclei (Section 5.1): grayscale morphological reconstruction by
+ * dilation of `marker` (J) under `mask` (I), the limit of
+ *     R_0 = min(J, I),  R_{k+1} = min(delta_conn(R_k), I)
+ * where delta_conn is the maximum over a pixel and its conn-neighbours
+ * (Vincent 1993). The paper runs it as an irregular wavefront propagation
+ * (IWPP) over active elements; `variant` picks how the GPU propagates
+ * (RT_RASTER, RT_QUEUE, RT_HYBRID, or RT_AUTO), with identical results.
+ *
+ * marker: uint8 H x W (ld_marker), or NULL: then the marker is derived on
+ *         the fly as in rt_marker with `h_offset`.
+ * mask:   uint8 H x W (ld_mask).
+ * out:    uint8 H x W (ld_out); may alias `marker` exactly (same pointer and
+ *         stride), must not overlap `mask`.
+ * A marker above the mask is clamped (R_0 = min(J, I)) and reported as
+ * RT_EMARKER in dev_status; the output is still the reconstruction of the
+ * clamped marker. An iteration bound hit is reported as RT_ETIMEOUT.
+ */
+RT_API rt_status rt_reconstruct(rt_ctx *ctx, const uint8_t *marker, int64_t ld_marker,
+                         const uint8_t *mask, int64_t ld_mask, uint8_t *out, int64_t ld_out,
+                         int H, int W, int conn, int variant, int h_offset,
+                         int32_t *dev_status, void *stream);
+
+/*
+ * FillHoles (Sections 3.2.1 and 5.1): out = 1 on the foreground of `in` and
+ * on every background pixel that no conn-connected path of background pixels
+ * links to the tile border (a hole); 0 on background reachable from the
+ * border. Equivalently 1 - R(M, C) with C = 1 - in and M = C on the border, 0
+ * elsewhere (reconstruction from the tile border).
+ * in: uint8 H x W (ld_in); out: uint8 H x W (ld_out), may alias `in` exactly.
+ */
+RT_API rt_status rt_fill_holes(rt_ctx *ctx, const uint8_t *in, int64_t ld_in, uint8_t *out,
+                        int64_t ld_out, int H, int W, int conn, int32_t *dev_status,
+                        void *stream);
+
+/*
+ * BWLabel (Section 5.1) + AreaThreshold (Section 3.2.1): labels of the
+ * conn-connected components of the foreground of `bin`. The label of a
+ * component is the smallest linear index r * W + c of its pixels (W, not the
+ * stride). Components whose pixel count lies outside [min_area, max_area]
+ * (both ends kept) and background pixels get -1. The GPU follows the
+ * union-find pattern the paper cites (a forest of pixel trees merged across
+ * neighbours, then flattened).
+ * bin: uint8 H x W (ld_bin); labels: int32 H x W (ld_lab), must not overlap bin.
+ * dev_n_kept (device int32, nullable) receives the number of components kept.
+ */
+RT_API rt_status rt_label_area(rt_ctx *ctx, const uint8_t *bin, int64_t ld_bin, int32_t *labels,
+                        int64_t ld_lab, int H, int W, int conn, int32_t min_area,
+                        int32_t max_area, int32_t *dev_n_kept, int32_t *dev_status,
+                        void *stream);
+
+/*
+ * Exact squared Euclidean distance transform, the input of the
+ * Pre-Watershed step (Section 5.1):
+ *     d2(p) = min over background pixels q of (r_p - r_q)^2 + (c_p - c_q)^2,
+ * background = (fg == 0); only in-image pixels count; 0 on the background;
+ * -1 everywhere if the image has no background pixel. Integer-exact.
+ * fg: uint8 H x W (ld_fg); d2: int32 H x W (ld_d2), must not overlap fg.
+ */
+RT_API rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int64_t ld_d2,
+                 int H, int W, int32_t *dev_status, void *stream);
+
+/* Phases of the library's launches, for the timing diagnostics below. */
+enum {
+    RT_PHASE_RECON_INIT = 0,   /* marker / padded copies of the mask */
+    RT_PHASE_RECON_SWEEP = 1,  /* propagation to the fixed point */
+    RT_PHASE_RECON_OUT = 2,    /* R output and threshold */
+    RT_PHASE_FILL = 3,         /* hole filling */
+    RT_PHASE_LABEL = 4,        /* labeling and area filter */
+    RT_PHASE_EDT = 5,          /* distance transform */
+    RT_NPHASES = 6
+};
+
+/*
+ * Timing diagnostics. With enable != 0 every phase of every later call is
+ * bracketed by CUDA events recorded on the call's stream. rt_timing_read
+ * waits for the recorded events, adds each phase's elapsed milliseconds to
+ * ms[phase] and its number of bracketed intervals to count[phase] (arrays of
+ * RT_NPHASES, either may be NULL), and forgets the records if reset != 0.
+ * rt_kernel_launches returns how many kernels the context has launched.
+ * rt_last_rounds waits for the device and returns the number of propagation
+ * rounds of the last reconstruction (statistics; 0 if none).
+ */
+RT_API rt_status rt_timing_enable(rt_ctx *ctx, int enable);
+RT_API rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset);
+RT_API int64_t rt_kernel_launches(const rt_ctx *ctx);
+RT_API int rt_last_rounds(rt_ctx *ctx);
+
+/* One tile of a batch. Every pointer is a device pointer. */
+typedef struct {
+    const uint8_t *img;   /* input tile I, uint8 H x W */
+    int64_t ld_img;
+    int H, W;
+    uint8_t *recon;       /* R, uint8 H x W; NULL = not returned */
+    int64_t ld_recon;
+    uint8_t *filled;      /* F, uint8 H x W; NULL = not returned */
+    int64_t ld_filled;
+    int32_t *labels;      /* L', int32 H x W (required) */
+    int64_t ld_labels;
+    int32_t *d2;          /* D, int32 H x W (required) */
+    int64_t ld_d2;
+    int32_t *n_kept;      /* device int32, nullable: components kept */
+    int32_t *status;      /* device int32, nullable: per-tile rt_status */
+} rt_tile;
+
+/* Parameters of the segmentation chain. */
+typedef struct {
+    int h_offset;    /* marker offset (30) */
+    int threshold;   /* B = (R < threshold) (80) */
+    int min_area;    /* area range kept, inclusive (20) */
+    int max_area;    /* (1000) */
+    int conn_recon;  /* connectivity of the reconstruction (8) */
+    int conn_fill;   /* connectivity of the background flood in fill-holes (4) */
+    int variant;     /* reconstruction variant for every tile (RT_AUTO) */
+    int max_rounds;  /* bound on propagation rounds per tile; 0 = default */
+} rt_seg_params;
+
+/* Fill `p` with the defaults listed above. */
+RT_API void rt_seg_params_default(rt_seg_params *p);
+
+/*
+ * The segmentation chain of the nuclei tiles on a batch of `n` tiles of
+ * possibly different sizes:
+ *   J = marker(I, h_offset); R = reconstruct(J, I, conn_recon);
+ *   B = (R < threshold); F = fill_holes(B, conn_fill);
+ *   L' = label_area(F, 8, [min_area, max_area]); D = edt(L' >= 0).
+ * `tiles` is a HOST array (copied before return); all outputs are device
+ * buffers. The per-tile outputs are identical to running the single-tile
+ * entry points one tile at a time.
+ */
+RT_API rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_seg_params *params,
+                           void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_SEG_H */

@@ -1,0 +1,247 @@
+"""GB300 (sm_103a) segmentation hot path of the Region Templates microscopy
+pipeline: reconstruction by dilation (ReconToNuclei), hole filling
+(FillHoles), connected-component labeling with an area filter (BWLabel +
+AreaThreshold) and the exact squared Euclidean distance transform (the
+Pre-Watershed input), behind the C ABI of include/rt.h.
+
+This module marshals torch CUDA tensors into the C ABI; torch provides device
+memory and streams only. All operations run in the library's own CUDA
+kernels. There is no CPU fallback: without the built library or a GPU every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _native
+from ._native import (RT_AUTO, RT_EINVAL, RT_EMARKER, RT_ETIMEOUT, RT_EUNAVAIL, RT_HYBRID, RT_OK,  # noqa: F401
+                      RT_QUEUE, RT_RASTER)
+
+__all__ = [
+    "Context", "SegParams", "marker", "reconstruct", "fill_holes", "label_area", "edt",
+    "segment_batch", "RT_AUTO", "RT_RASTER", "RT_QUEUE", "RT_HYBRID",
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _native.load()
+    return _lib
+
+
+class RtError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {lib().rt_status_str(code).decode()} (code {code})")
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != RT_OK:
+        raise RtError(code, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dev_ptr(t: torch.Tensor, dtype: torch.dtype, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or t.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D {dtype} tensor")
+    if t.stride(1) != 1:
+        raise ValueError(f"{name} must have unit column stride")
+    return t.data_ptr(), t.stride(0)
+
+
+class Context:
+    """Owns a library context (device workspace) on one CUDA device."""
+
+    def __init__(self, device: int | None = None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(lib().rt_create(ctypes.byref(h), device), "rt_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self) -> int:
+        return lib().rt_workspace_bytes(self._h)
+
+    def timing(self, enable: bool = True):
+        _check(lib().rt_timing_enable(self._h, int(enable)), "rt_timing_enable")
+
+    def read_timing(self, reset: bool = True) -> dict:
+        """Per-phase {name: (milliseconds, intervals)} since the last reset."""
+        ms = (ctypes.c_double * _native.RT_NPHASES)()
+        cnt = (ctypes.c_int64 * _native.RT_NPHASES)()
+        _check(lib().rt_timing_read(self._h, ms, cnt, int(reset)), "rt_timing_read")
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(_native.PHASES)}
+
+    def kernel_launches(self) -> int:
+        return lib().rt_kernel_launches(self._h)
+
+    def last_rounds(self) -> int:
+        return lib().rt_last_rounds(self._h)
+
+    def close(self):
+        if self._h:
+            lib().rt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default = {}
+
+
+def default_context(device: int | None = None) -> Context:
+    if device is None:
+        device = torch.cuda.current_device()
+    if device not in _default:
+        _default[device] = Context(device)
+    return _default[device]
+
+
+def marker(mask: torch.Tensor, h_offset: int = 30, out=None, ctx=None, stream=None) -> torch.Tensor:
+    ctx = ctx or default_context(mask.device.index)
+    mp, mld = _dev_ptr(mask, torch.uint8, "mask")
+    H, W = mask.shape
+    out = torch.empty_like(mask, memory_format=torch.contiguous_format) if out is None else out
+    op, old = _dev_ptr(out, torch.uint8, "out")
+    _check(lib().rt_marker(ctx.handle, mp, mld, op, old, H, W, h_offset, _stream(stream)), "rt_marker")
+    return out
+
+
+def reconstruct(mask: torch.Tensor, marker: torch.Tensor | None = None, *, h_offset: int = 30, conn: int = 8,
+                variant: int = RT_AUTO, out=None, status=None, ctx=None, stream=None) -> torch.Tensor:
+    """Reconstruction by dilation of `marker` under `mask` (uint8 CUDA
+    tensors). marker=None derives it from the mask with h_offset."""
+    ctx = ctx or default_context(mask.device.index)
+    ip, ild = _dev_ptr(mask, torch.uint8, "mask")
+    H, W = mask.shape
+    jp, jld = (None, 0) if marker is None else _dev_ptr(marker, torch.uint8, "marker")
+    out = torch.empty((H, W), dtype=torch.uint8, device=mask.device) if out is None else out
+    op, old = _dev_ptr(out, torch.uint8, "out")
+    sp = None if status is None else status.data_ptr()
+    _check(lib().rt_reconstruct(ctx.handle, jp, jld, ip, ild, op, old, H, W, conn, variant, h_offset, sp,
+                                _stream(stream)), "rt_reconstruct")
+    return out
+
+
+def fill_holes(binary: torch.Tensor, *, conn: int = 4, out=None, status=None, ctx=None, stream=None):
+    ctx = ctx or default_context(binary.device.index)
+    bp, bld = _dev_ptr(binary, torch.uint8, "binary")
+    H, W = binary.shape
+    out = torch.empty((H, W), dtype=torch.uint8, device=binary.device) if out is None else out
+    op, old = _dev_ptr(out, torch.uint8, "out")
+    sp = None if status is None else status.data_ptr()
+    _check(lib().rt_fill_holes(ctx.handle, bp, bld, op, old, H, W, conn, sp, _stream(stream)), "rt_fill_holes")
+    return out
+
+
+def label_area(binary: torch.Tensor, min_area: int = 20, max_area: int = 1000, *, conn: int = 8, out=None,
+               n_kept=None, status=None, ctx=None, stream=None):
+    ctx = ctx or default_context(binary.device.index)
+    bp, bld = _dev_ptr(binary, torch.uint8, "binary")
+    H, W = binary.shape
+    out = torch.empty((H, W), dtype=torch.int32, device=binary.device) if out is None else out
+    op, old = _dev_ptr(out, torch.int32, "out")
+    kp = None if n_kept is None else n_kept.data_ptr()
+    sp = None if status is None else status.data_ptr()
+    _check(lib().rt_label_area(ctx.handle, bp, bld, op, old, H, W, conn, min_area, max_area, kp, sp,
+                               _stream(stream)), "rt_label_area")
+    return out
+
+
+def edt(fg: torch.Tensor, *, out=None, status=None, ctx=None, stream=None):
+    ctx = ctx or default_context(fg.device.index)
+    fp, fld = _dev_ptr(fg, torch.uint8, "fg")
+    H, W = fg.shape
+    out = torch.empty((H, W), dtype=torch.int32, device=fg.device) if out is None else out
+    op, old = _dev_ptr(out, torch.int32, "out")
+    sp = None if status is None else status.data_ptr()
+    _check(lib().rt_edt(ctx.handle, fp, fld, op, old, H, W, sp, _stream(stream)), "rt_edt")
+    return out
+
+
+@dataclass
+class SegParams:
+    h_offset: int = 30
+    threshold: int = 80
+    min_area: int = 20
+    max_area: int = 1000
+    conn_recon: int = 8
+    conn_fill: int = 4
+    variant: int = RT_AUTO
+    max_rounds: int = 0
+
+    def to_c(self) -> _native.RtSegParams:
+        p = _native.RtSegParams()
+        for k in self.__dataclass_fields__:
+            setattr(p, k, int(getattr(self, k)))
+        return p
+
+
+def segment_batch(images, params: SegParams | None = None, *, outputs=None, want_recon: bool = True,
+                  want_filled: bool = True, ctx=None, stream=None):
+    """Run the segmentation chain on a list of uint8 CUDA tiles. Returns a list
+    of dicts with R, F (if requested), L, D, n_kept and status tensors. Pass
+    `outputs` (a list from a previous call) to reuse the buffers."""
+    if not images:
+        return []
+    ctx = ctx or default_context(images[0].device.index)
+    params = params or SegParams()
+    n = len(images)
+    tiles = (_native.RtTile * n)()
+    if outputs is None:
+        outputs = []
+        for img in images:
+            H, W = img.shape
+            dev = img.device
+            o = {
+                "L": torch.empty((H, W), dtype=torch.int32, device=dev),
+                "D": torch.empty((H, W), dtype=torch.int32, device=dev),
+                "n_kept": torch.zeros(1, dtype=torch.int32, device=dev),
+                "status": torch.zeros(1, dtype=torch.int32, device=dev),
+            }
+            if want_recon:
+                o["R"] = torch.empty((H, W), dtype=torch.uint8, device=dev)
+            if want_filled:
+                o["F"] = torch.empty((H, W), dtype=torch.uint8, device=dev)
+            outputs.append(o)
+    for i, (img, o) in enumerate(zip(images, outputs)):
+        ip, ild = _dev_ptr(img, torch.uint8, "image")
+        t = tiles[i]
+        t.img, t.ld_img = ip, ild
+        t.H, t.W = img.shape
+        if "R" in o:
+            t.recon, t.ld_recon = _dev_ptr(o["R"], torch.uint8, "R")
+        if "F" in o:
+            t.filled, t.ld_filled = _dev_ptr(o["F"], torch.uint8, "F")
+        t.labels, t.ld_labels = _dev_ptr(o["L"], torch.int32, "L")
+        t.d2, t.ld_d2 = _dev_ptr(o["D"], torch.int32, "D")
+        t.n_kept = o["n_kept"].data_ptr()
+        t.status = o["status"].data_ptr()
+    cp = params.to_c()
+    _check(lib().rt_segment_batch(ctx.handle, tiles, n, ctypes.byref(cp), _stream(stream)), "rt_segment_batch")
+    return outputs

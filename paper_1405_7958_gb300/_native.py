@@ -1,0 +1,83 @@
+"""ctypes binding of librtseg.so: the C ABI declared in include/rt.h, with the
+same function names. Argument marshalling only -- every step of the path runs
+in the library's CUDA kernels. Importing this module raises if the library has
+not been built: there is no CPU fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librtseg.so")
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT, RT_EMARKER, RT_EQUEUE, RT_EUNAVAIL = range(8)
+RT_AUTO, RT_RASTER, RT_QUEUE, RT_HYBRID = range(4)
+
+# every symbol declared in include/rt.h
+EXPORTS = (
+    "rt_create", "rt_destroy", "rt_status_str", "rt_version", "rt_workspace_bytes", "rt_marker",
+    "rt_reconstruct", "rt_fill_holes", "rt_label_area", "rt_edt", "rt_seg_params_default",
+    "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_last_rounds",
+)
+RT_NPHASES = 6
+PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt")
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_int = ctypes.c_int
+
+
+class RtTile(ctypes.Structure):
+    _fields_ = [
+        ("img", _vp), ("ld_img", _i64), ("H", _int), ("W", _int),
+        ("recon", _vp), ("ld_recon", _i64),
+        ("filled", _vp), ("ld_filled", _i64),
+        ("labels", _vp), ("ld_labels", _i64),
+        ("d2", _vp), ("ld_d2", _i64),
+        ("n_kept", _vp), ("status", _vp),
+    ]
+
+
+class RtSegParams(ctypes.Structure):
+    _fields_ = [(n, _int) for n in ("h_offset", "threshold", "min_area", "max_area", "conn_recon",
+                                    "conn_fill", "variant", "max_rounds")]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"librtseg.so is not built ({path}); run paper_1405_7958_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    lib.rt_create.argtypes = [ctypes.POINTER(_vp), _int]
+    lib.rt_create.restype = _int
+    lib.rt_destroy.argtypes = [_vp]
+    lib.rt_destroy.restype = None
+    lib.rt_status_str.argtypes = [_int]
+    lib.rt_status_str.restype = ctypes.c_char_p
+    lib.rt_version.argtypes = []
+    lib.rt_version.restype = _int
+    lib.rt_workspace_bytes.argtypes = [_vp]
+    lib.rt_workspace_bytes.restype = ctypes.c_size_t
+    lib.rt_marker.argtypes = [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _vp]
+    lib.rt_marker.restype = _int
+    lib.rt_reconstruct.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _int, _int, _int, _int, _int, _vp, _vp]
+    lib.rt_reconstruct.restype = _int
+    lib.rt_fill_holes.argtypes = [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _vp, _vp]
+    lib.rt_fill_holes.restype = _int
+    lib.rt_label_area.argtypes = [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _i32, _i32, _vp, _vp, _vp]
+    lib.rt_label_area.restype = _int
+    lib.rt_edt.argtypes = [_vp, _vp, _i64, _vp, _i64, _int, _int, _vp, _vp]
+    lib.rt_edt.restype = _int
+    lib.rt_seg_params_default.argtypes = [ctypes.POINTER(RtSegParams)]
+    lib.rt_seg_params_default.restype = None
+    lib.rt_segment_batch.argtypes = [_vp, ctypes.POINTER(RtTile), _int, ctypes.POINTER(RtSegParams), _vp]
+    lib.rt_segment_batch.restype = _int
+    lib.rt_timing_enable.argtypes = [_vp, _int]
+    lib.rt_timing_enable.restype = _int
+    lib.rt_timing_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _int]
+    lib.rt_timing_read.restype = _int
+    lib.rt_kernel_launches.argtypes = [_vp]
+    lib.rt_kernel_launches.restype = _i64
+    lib.rt_last_rounds.argtypes = [_vp]
+    lib.rt_last_rounds.restype = _int
+    return lib

@@ -1,0 +1,611 @@
+// C-ABI entry points of the segmentation library (declared in rt.h):
+// argument validation, the context and its device workspace, and the
+// launch sequence of every operation and of the segmentation chain.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ccl.cuh"
+#include "common.cuh"
+#include "edt.cuh"
+#include "recon.cuh"
+
+using namespace rtk;
+
+struct PhaseRec {
+    int phase;
+    cudaEvent_t a, b;
+};
+
+struct rt_ctx {
+    int device = 0;
+    int num_sms = 0;
+    void *ws = nullptr;       // device workspace
+    size_t ws_bytes = 0;
+    int32_t *rounds_dev = nullptr;   // rounds of the last reconstruction (in the workspace)
+    int64_t launches = 0;     // kernels launched
+    bool timing = false;
+    std::vector<PhaseRec> recs;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+cudaEvent_t take_event(rt_ctx *ctx)
+{
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one phase with events on the stream when timing is enabled.
+class Phase {
+  public:
+    Phase(rt_ctx *ctx, int phase, cudaStream_t s) : ctx_(ctx), s_(s)
+    {
+        if (!ctx->timing) return;
+        rec_.phase = phase;
+        rec_.a = take_event(ctx);
+        rec_.b = take_event(ctx);
+        cudaEventRecord(rec_.a, s);
+    }
+    ~Phase()
+    {
+        if (!ctx_->timing || !rec_.a) return;
+        cudaEventRecord(rec_.b, s_);
+        ctx_->recs.push_back(rec_);
+    }
+
+  private:
+    rt_ctx *ctx_;
+    cudaStream_t s_;
+    PhaseRec rec_{0, nullptr, nullptr};
+};
+
+constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s per barrier wait
+
+// Bump allocator over the context workspace (256-byte aligned pieces).
+struct Carve {
+    size_t off = 0;
+    char *base = nullptr;
+    template <class T>
+    T *take(size_t count)
+    {
+        off = (size_t)round_up((int64_t)off, 256);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+        dev_ = dev;
+    }
+    ~DeviceGuard()
+    {
+        if (prev_ != dev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = 0, dev_ = 0;
+};
+
+rt_status ensure_ws(rt_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->ws_bytes) return RT_OK;
+    if (ctx->ws) {
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+        ctx->rounds_dev = nullptr;
+    }
+    size_t want = (size_t)round_up((int64_t)bytes, 1 << 20);
+    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return RT_ENOMEM;
+    }
+    ctx->ws_bytes = want;
+    return RT_OK;
+}
+
+bool bad_dims(int H, int W) { return H < 1 || W < 1 || H > kMaxSide || W > kMaxSide; }
+
+bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+size_t span(int H, int64_t ld, size_t elem, int W) { return ((size_t)(H - 1) * ld + W) * elem; }
+
+rt_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return RT_OK;
+    cudaGetLastError();
+    return RT_ECUDA;
+}
+
+// ---------------------------------------------------------------- recon
+struct ReconWs {
+    uint8_t *active;
+    uint32_t *ctl;     // counters[3], bar[2]
+    int32_t *err;
+    int32_t *rounds;
+};
+
+// Reserve the sweep control block and per-image padded buffers.
+void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w)
+{
+    w.active = cv.take<uint8_t>((size_t)2 * b.ntiles);
+    w.ctl = cv.take<uint32_t>(8);
+    w.err = cv.take<int32_t>(1);
+    w.rounds = cv.take<int32_t>(1);
+    for (int i = 0; i < b.n; ++i) {
+        ReconImage &d = b.img[i];
+        d.Rw = cv.take<uint8_t>((size_t)d.Hp * d.Wp);
+        d.Iw = cv.take<uint8_t>((size_t)d.Hp * d.Wp);
+    }
+}
+
+// Enqueue init + sweeps for a batch whose buffers are carved. `err` receives
+// the device status.
+rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int max_rounds, int32_t *err,
+                    cudaStream_t s)
+{
+    // round 0 visits every tile; flags of round 1 start clear
+    RT_CUDA_TRY(cudaMemsetAsync(w.active, 1, (size_t)b.ntiles, s));
+    RT_CUDA_TRY(cudaMemsetAsync(w.active + b.ntiles, 0, (size_t)b.ntiles, s));
+    RT_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, 8 * sizeof(uint32_t), s));
+    {
+        Phase ph(ctx, RT_PHASE_RECON_INIT, s);
+        RT_CUDA_TRY(launch_recon_init(b, err, s));
+        ctx->launches += 1;
+    }
+    ctx->rounds_dev = w.rounds;
+    SweepParams p;
+    p.b = b;
+    p.ntiles = b.ntiles;
+    p.active = w.active;
+    p.counters = w.ctl;
+    p.bar = w.ctl + 4;
+    p.err = err;
+    p.rounds_out = w.rounds;
+    p.max_rounds = max_rounds > 0 ? max_rounds : 1 << 20;
+    p.timeout_ns = kBarrierTimeoutNs;
+    int grid = 0;
+    Phase ph(ctx, RT_PHASE_RECON_SWEEP, s);
+    ctx->launches += 1;
+    return cuda_status(launch_recon_sweep(p, conn, ctx->num_sms, s, &grid));
+}
+
+void add_image(ReconBatch &b, const uint8_t *marker, int64_t ld_marker, const uint8_t *mask, int64_t ld_mask,
+               int H, int W, int h_offset)
+{
+    ReconImage &d = b.img[b.n];
+    std::memset(&d, 0, sizeof(d));
+    d.marker = marker;
+    d.ld_marker = ld_marker;
+    d.mask = mask;
+    d.ld_mask = ld_mask;
+    d.h_offset = h_offset;
+    plan_recon_image(d, H, W);
+    d.tile_base = b.ntiles;
+    b.ntiles += d.tiles_x * d.tiles_y;
+    const int64_t words = (int64_t)d.Hp * d.Wp / 4;
+    if (words > b.max_words) b.max_words = words;
+    b.n++;
+}
+
+__global__ void copy_status_kernel(const int32_t *src, int32_t *dst)
+{
+    if (threadIdx.x == 0 && *src != 0) atomicCAS(dst, 0, *src);
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+extern "C" {
+
+int rt_version(void) { return 100; }
+
+const char *rt_status_str(int status)
+{
+    switch (status) {
+    case RT_OK: return "RT_OK";
+    case RT_EINVAL: return "RT_EINVAL: invalid argument";
+    case RT_ENOMEM: return "RT_ENOMEM: device workspace allocation failed";
+    case RT_ECUDA: return "RT_ECUDA: CUDA runtime error";
+    case RT_ETIMEOUT: return "RT_ETIMEOUT: device iteration or wait bound reached";
+    case RT_EMARKER: return "RT_EMARKER: marker above mask (clamped)";
+    case RT_EQUEUE: return "RT_EQUEUE: frontier queue overflow";
+    case RT_EUNAVAIL: return "RT_EUNAVAIL: variant or feature unavailable";
+    default: return "unknown rt_status";
+    }
+}
+
+rt_status rt_create(rt_ctx **ctx, int device)
+{
+    if (!ctx) return RT_EINVAL;
+    *ctx = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return RT_ECUDA;
+    }
+    rt_ctx *c = new (std::nothrow) rt_ctx;
+    if (!c) return RT_ENOMEM;
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return RT_ECUDA;
+    }
+    *ctx = c;
+    return RT_OK;
+}
+
+void rt_destroy(rt_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    if (ctx->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+    }
+    for (const PhaseRec &r : ctx->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+size_t rt_workspace_bytes(const rt_ctx *ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+rt_status rt_timing_enable(rt_ctx *ctx, int enable)
+{
+    if (!ctx) return RT_EINVAL;
+    ctx->timing = enable != 0;
+    return RT_OK;
+}
+
+rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset)
+{
+    if (!ctx) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    for (const PhaseRec &r : ctx->recs) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) {
+            cudaGetLastError();
+            return RT_ECUDA;
+        }
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            return RT_ECUDA;
+        }
+        if (r.phase >= 0 && r.phase < RT_NPHASES) {
+            if (ms) ms[r.phase] += t;
+            if (count) count[r.phase] += 1;
+        }
+    }
+    if (reset) {
+        for (const PhaseRec &r : ctx->recs) {
+            ctx->pool.push_back(r.a);
+            ctx->pool.push_back(r.b);
+        }
+        ctx->recs.clear();
+    }
+    return RT_OK;
+}
+
+int64_t rt_kernel_launches(const rt_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int rt_last_rounds(rt_ctx *ctx)
+{
+    if (!ctx || !ctx->rounds_dev) return 0;
+    DeviceGuard g(ctx->device);
+    int32_t v = 0;
+    if (cudaMemcpy(&v, ctx->rounds_dev, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
+
+rt_status rt_marker(rt_ctx *ctx, const uint8_t *mask, int64_t ld_mask, uint8_t *marker, int64_t ld_marker, int H,
+                    int W, int h_offset, void *stream)
+{
+    if (!ctx || !mask || !marker || bad_dims(H, W) || ld_mask < W || ld_marker < W || h_offset < 0 ||
+        h_offset > 255)
+        return RT_EINVAL;
+    if (overlaps(mask, span(H, ld_mask, 1, W), marker, span(H, ld_marker, 1, W))) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    Phase ph(ctx, RT_PHASE_RECON_INIT, (cudaStream_t)stream);
+    ctx->launches += 1;
+    return cuda_status(launch_marker(mask, ld_mask, marker, ld_marker, H, W, h_offset, (cudaStream_t)stream));
+}
+
+rt_status rt_reconstruct(rt_ctx *ctx, const uint8_t *marker, int64_t ld_marker, const uint8_t *mask,
+                         int64_t ld_mask, uint8_t *out, int64_t ld_out, int H, int W, int conn, int variant,
+                         int h_offset, int32_t *dev_status, void *stream)
+{
+    if (!ctx || !mask || !out || bad_dims(H, W) || ld_mask < W || ld_out < W) return RT_EINVAL;
+    if (conn != 4 && conn != 8) return RT_EINVAL;
+    if (variant < RT_AUTO || variant > RT_HYBRID) return RT_EINVAL;
+    if (marker && ld_marker < W) return RT_EINVAL;
+    if (!marker && (h_offset < 0 || h_offset > 255)) return RT_EINVAL;
+    if (overlaps(out, span(H, ld_out, 1, W), mask, span(H, ld_mask, 1, W))) return RT_EINVAL;
+    if (marker && marker != out && overlaps(out, span(H, ld_out, 1, W), marker, span(H, ld_marker, 1, W)))
+        return RT_EINVAL;
+    if (marker && marker == out && ld_marker != ld_out) return RT_EINVAL;
+    if (variant == RT_QUEUE || variant == RT_HYBRID) return RT_EUNAVAIL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    ReconBatch b;
+    std::memset(&b, 0, sizeof(b));
+    add_image(b, marker, ld_marker, mask, ld_mask, H, W, h_offset);
+    Carve cv;
+    ReconWs w;
+    carve_recon(cv, b, w);
+    rt_status st = ensure_ws(ctx, cv.off);
+    if (st != RT_OK) return st;
+    cv = Carve();
+    cv.base = (char *)ctx->ws;
+    carve_recon(cv, b, w);
+
+    int32_t *err = dev_status ? dev_status : w.err;
+    RT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    st = run_recon(ctx, b, w, conn, 0, err, s);
+    if (st != RT_OK) return st;
+    Phase ph(ctx, RT_PHASE_RECON_OUT, s);
+    ctx->launches += 1;
+    return cuda_status(launch_recon_out(b.img[0].Rw, b.img[0].Wp, out, ld_out, H, W, nullptr, 0, 0, s));
+}
+
+rt_status rt_fill_holes(rt_ctx *ctx, const uint8_t *in, int64_t ld_in, uint8_t *out, int64_t ld_out, int H, int W,
+                        int conn, int32_t *dev_status, void *stream)
+{
+    if (!ctx || !in || !out || bad_dims(H, W) || ld_in < W || ld_out < W) return RT_EINVAL;
+    if (conn != 4 && conn != 8) return RT_EINVAL;
+    if ((const void *)in != (const void *)out && overlaps(in, span(H, ld_in, 1, W), out, span(H, ld_out, 1, W)))
+        return RT_EINVAL;
+    if ((const void *)in == (const void *)out && ld_in != ld_out) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)H * W;
+    Carve cv;
+    cv.take<int32_t>(N);
+    cv.take<int32_t>(N);
+    rt_status st = ensure_ws(ctx, cv.off);
+    if (st != RT_OK) return st;
+    cv = Carve();
+    cv.base = (char *)ctx->ws;
+    UfArgs a;
+    a.in = in;
+    a.ld_in = ld_in;
+    a.H = H;
+    a.W = W;
+    a.U = cv.take<int32_t>(N);
+    a.A = cv.take<int32_t>(N);
+    if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
+    Phase ph(ctx, RT_PHASE_FILL, s);
+    ctx->launches += 4;
+    RT_CUDA_TRY(uf_build(a, conn, kFgZero, false, true, s));
+    return cuda_status(uf_fill_out(a, out, ld_out, s));
+}
+
+rt_status rt_label_area(rt_ctx *ctx, const uint8_t *bin, int64_t ld_bin, int32_t *labels, int64_t ld_lab, int H,
+                        int W, int conn, int32_t min_area, int32_t max_area, int32_t *dev_n_kept,
+                        int32_t *dev_status, void *stream)
+{
+    if (!ctx || !bin || !labels || bad_dims(H, W) || ld_bin < W || ld_lab < W) return RT_EINVAL;
+    if (conn != 4 && conn != 8) return RT_EINVAL;
+    if (overlaps(bin, span(H, ld_bin, 1, W), labels, span(H, ld_lab, 4, W))) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)H * W;
+    Carve cv;
+    cv.take<int32_t>(N);
+    cv.take<int32_t>(N);
+    rt_status st = ensure_ws(ctx, cv.off);
+    if (st != RT_OK) return st;
+    cv = Carve();
+    cv.base = (char *)ctx->ws;
+    UfArgs a;
+    a.in = bin;
+    a.ld_in = ld_bin;
+    a.H = H;
+    a.W = W;
+    a.U = cv.take<int32_t>(N);
+    a.A = cv.take<int32_t>(N);
+    if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
+    if (dev_n_kept) RT_CUDA_TRY(cudaMemsetAsync(dev_n_kept, 0, sizeof(int32_t), s));
+    Phase ph(ctx, RT_PHASE_LABEL, s);
+    ctx->launches += 4;
+    RT_CUDA_TRY(uf_build(a, conn, kFgNonzero, true, false, s));
+    return cuda_status(uf_labels_out(a, labels, ld_lab, min_area, max_area, dev_n_kept, s));
+}
+
+rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int64_t ld_d2, int H, int W,
+                 int32_t *dev_status, void *stream)
+{
+    if (!ctx || !fg || !d2 || bad_dims(H, W) || ld_fg < W || ld_d2 < W) return RT_EINVAL;
+    if (overlaps(fg, span(H, ld_fg, 1, W), d2, span(H, ld_d2, 4, W))) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Carve cv;
+    cv.take<char>(edt_workspace_bytes(H, W));
+    rt_status st = ensure_ws(ctx, cv.off + 1024);
+    if (st != RT_OK) return st;
+    cv = Carve();
+    cv.base = (char *)ctx->ws;
+    EdtArgs a;
+    a.fg8 = fg;
+    a.lab32 = nullptr;
+    a.ld_in = ld_fg;
+    a.H = H;
+    a.W = W;
+    a.d2 = d2;
+    a.ld_d2 = ld_d2;
+    a.g = cv.take<uint16_t>((size_t)H * W);
+    a.seg = cv.take<int32_t>((size_t)2 * ceil_div(H, 32) * W);
+    a.any_bg = cv.take<uint32_t>(1);
+    if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
+    Phase ph(ctx, RT_PHASE_EDT, s);
+    ctx->launches += 3;
+    return cuda_status(launch_edt(a, s));
+}
+
+void rt_seg_params_default(rt_seg_params *p)
+{
+    if (!p) return;
+    p->h_offset = 30;
+    p->threshold = 80;
+    p->min_area = 20;
+    p->max_area = 1000;
+    p->conn_recon = 8;
+    p->conn_fill = 4;
+    p->variant = RT_AUTO;
+    p->max_rounds = 0;
+}
+
+rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_seg_params *params, void *stream)
+{
+    if (!ctx || (!tiles && n > 0) || n < 0 || !params) return RT_EINVAL;
+    const rt_seg_params &P = *params;
+    if (P.conn_recon != 4 && P.conn_recon != 8) return RT_EINVAL;
+    if (P.conn_fill != 4 && P.conn_fill != 8) return RT_EINVAL;
+    if (P.h_offset < 0 || P.h_offset > 255 || P.threshold < 0 || P.threshold > 256) return RT_EINVAL;
+    if (P.variant < RT_AUTO || P.variant > RT_HYBRID) return RT_EINVAL;
+    if (P.variant == RT_QUEUE || P.variant == RT_HYBRID) return RT_EUNAVAIL;
+    int64_t maxN = 0;
+    for (int i = 0; i < n; ++i) {
+        const rt_tile &t = tiles[i];
+        if (!t.img || !t.labels || !t.d2 || bad_dims(t.H, t.W)) return RT_EINVAL;
+        if (t.ld_img < t.W || t.ld_labels < t.W || t.ld_d2 < t.W) return RT_EINVAL;
+        if (t.recon && t.ld_recon < t.W) return RT_EINVAL;
+        if (t.filled && t.ld_filled < t.W) return RT_EINVAL;
+        if ((int64_t)t.H * t.W > maxN) maxN = (int64_t)t.H * t.W;
+    }
+    if (n == 0) return RT_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    for (int c0 = 0; c0 < n; c0 += kMaxImgs) {
+        const int cn = n - c0 < kMaxImgs ? n - c0 : kMaxImgs;
+        ReconBatch b;
+        std::memset(&b, 0, sizeof(b));
+        for (int i = 0; i < cn; ++i) {
+            const rt_tile &t = tiles[c0 + i];
+            add_image(b, nullptr, 0, t.img, t.ld_img, t.H, t.W, P.h_offset);
+        }
+        // workspace: recon buffers for the chunk, binary B per tile, then one
+        // shared set of union-find / EDT buffers (tiles run one after another)
+        auto layout = [&](Carve &cv, ReconWs &w, std::vector<uint8_t *> &Bs, uint8_t *&Fw, int32_t *&U,
+                          int32_t *&A, char *&edt_ws) {
+            carve_recon(cv, b, w);
+            Bs.resize(cn);
+            for (int i = 0; i < cn; ++i) Bs[i] = cv.take<uint8_t>((size_t)b.img[i].H * b.img[i].W);
+            Fw = cv.take<uint8_t>((size_t)maxN);
+            U = cv.take<int32_t>((size_t)maxN);
+            A = cv.take<int32_t>((size_t)maxN);
+            int maxH = 0, maxW = 0;
+            for (int i = 0; i < cn; ++i) {
+                maxH = b.img[i].H > maxH ? b.img[i].H : maxH;
+                maxW = b.img[i].W > maxW ? b.img[i].W : maxW;
+            }
+            edt_ws = cv.take<char>(edt_workspace_bytes(maxH, maxW) + (size_t)maxN * 2);
+        };
+        Carve cv;
+        ReconWs w;
+        std::vector<uint8_t *> Bs;
+        uint8_t *Fw;
+        int32_t *U, *A;
+        char *edt_ws;
+        layout(cv, w, Bs, Fw, U, A, edt_ws);
+        rt_status st = ensure_ws(ctx, cv.off);
+        if (st != RT_OK) return st;
+        cv = Carve();
+        cv.base = (char *)ctx->ws;
+        layout(cv, w, Bs, Fw, U, A, edt_ws);
+
+        RT_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
+        st = run_recon(ctx, b, w, P.conn_recon, P.max_rounds, w.err, s);
+        if (st != RT_OK) return st;
+        for (int i = 0; i < cn; ++i) {
+            const rt_tile &t = tiles[c0 + i];
+            const ReconImage &d = b.img[i];
+            const int H = t.H, W = t.W;
+            {
+                Phase ph(ctx, RT_PHASE_RECON_OUT, s);
+                ctx->launches += 1;
+                RT_CUDA_TRY(launch_recon_out(d.Rw, d.Wp, t.recon, t.ld_recon, H, W, Bs[i], W, P.threshold, s));
+            }
+            UfArgs fa;
+            fa.in = Bs[i];
+            fa.ld_in = W;
+            fa.H = H;
+            fa.W = W;
+            fa.U = U;
+            fa.A = A;
+            uint8_t *F = t.filled ? t.filled : Fw;
+            const int64_t ldF = t.filled ? t.ld_filled : W;
+            {
+                Phase ph(ctx, RT_PHASE_FILL, s);
+                ctx->launches += 4;
+                RT_CUDA_TRY(uf_build(fa, P.conn_fill, kFgZero, false, true, s));
+                RT_CUDA_TRY(uf_fill_out(fa, F, ldF, s));
+            }
+            UfArgs la = fa;
+            la.in = F;
+            la.ld_in = ldF;
+            if (t.n_kept) RT_CUDA_TRY(cudaMemsetAsync(t.n_kept, 0, sizeof(int32_t), s));
+            {
+                Phase ph(ctx, RT_PHASE_LABEL, s);
+                ctx->launches += 4;
+                RT_CUDA_TRY(uf_build(la, 8, kFgNonzero, true, false, s));
+                RT_CUDA_TRY(uf_labels_out(la, t.labels, t.ld_labels, P.min_area, P.max_area, t.n_kept, s));
+            }
+            EdtArgs ea;
+            ea.fg8 = nullptr;
+            ea.lab32 = t.labels;
+            ea.ld_in = t.ld_labels;
+            ea.H = H;
+            ea.W = W;
+            ea.d2 = t.d2;
+            ea.ld_d2 = t.ld_d2;
+            Carve ec;
+            ec.base = edt_ws;
+            ea.g = ec.take<uint16_t>((size_t)H * W);
+            ea.seg = ec.take<int32_t>((size_t)2 * ceil_div(H, 32) * W);
+            ea.any_bg = ec.take<uint32_t>(1);
+            {
+                Phase ph(ctx, RT_PHASE_EDT, s);
+                ctx->launches += 3;
+                RT_CUDA_TRY(launch_edt(ea, s));
+            }
+            if (t.status) {
+                RT_CUDA_TRY(cudaMemsetAsync(t.status, 0, sizeof(int32_t), s));
+                copy_status_kernel<<<1, 32, 0, s>>>(w.err, t.status);
+                ctx->launches += 1;
+                RT_CUDA_TRY(cudaGetLastError());
+            }
+        }
+    }
+    return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,276 @@
+// BWLabel (Section 5.1) and FillHoles (Sections 3.2.1, 5.1) by union-find.
+//
+// The paper's BWLabel follows the union-find pattern: every pixel starts as
+// its own tree, trees of adjacent foreground pixels are merged, and labels
+// are read off by flattening the trees. Merging always hooks the root with
+// the larger linear index under the smaller one (atomicMin on the parent),
+// so the root of a finished tree is the smallest index of its component:
+// the canonical label. The forest is built in two levels:
+//   1. each 32 x 32 block merges its own pixels in shared memory and writes
+//      for every pixel the (global) index of its block-local root;
+//   2. pixel pairs that straddle a block edge are merged in global memory;
+//   3. flattening points every pixel at its final root and accumulates, per
+//      root, the component area (labeling) or whether the component touches
+//      the image border (hole filling: the background components are built
+//      and the ones that do not touch the border are holes).
+#include "ccl.cuh"
+
+namespace rtk {
+
+constexpr int kB = 32;          // block side
+constexpr int kRowsPerThread = 4;
+
+__device__ __forceinline__ bool is_fg(const uint8_t *in, int64_t ld, int r, int c, int source)
+{
+    const uint8_t v = in[(int64_t)r * ld + c];
+    return source == kFgNonzero ? v != 0 : v == 0;
+}
+
+// --------------------------------------------------- shared-memory forest
+__device__ __forceinline__ int find_s(volatile int *P, int x)
+{
+    int p = P[x];
+    while (p != x) {
+        x = p;
+        p = P[x];
+    }
+    return x;
+}
+
+__device__ __forceinline__ void union_s(int *P, int a, int b)
+{
+    volatile int *VP = P;
+    for (;;) {
+        a = find_s(VP, a);
+        b = find_s(VP, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a; a = b; b = t;
+        }
+        // a > b: hook a under b
+        const int old = atomicMin(P + a, b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+// ---------------------------------------------------- global forest
+__device__ __forceinline__ int32_t find_g(const int32_t *U, int32_t x)
+{
+    int32_t p = ld_relaxed_i32(U + x);
+    while (p != x) {
+        x = p;
+        p = ld_relaxed_i32(U + x);
+    }
+    return x;
+}
+
+__device__ __forceinline__ void union_g(int32_t *U, int32_t a, int32_t b)
+{
+    for (;;) {
+        a = find_g(U, a);
+        b = find_g(U, b);
+        if (a == b) return;
+        if (a < b) {
+            const int32_t t = a; a = b; b = t;
+        }
+        const int32_t old = atomicMin(U + a, b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+// 1. block-local forests. Block of 32 x 32 pixels, 256 threads: thread
+// (tx, ty) owns column tx, rows 4*ty .. 4*ty+3.
+template <int CONN>
+__global__ void __launch_bounds__(256) uf_local_kernel(UfArgs a, int source, bool zero_acc)
+{
+    __shared__ int P[kB * kB];
+    __shared__ uint8_t F[kB * kB];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        const int lr = ty * kRowsPerThread + k;
+        const int r = r0 + lr, c = c0 + tx;
+        const bool f = (r < a.H && c < a.W) && is_fg(a.in, a.ld_in, r, c, source);
+        F[lr * kB + tx] = f;
+        P[lr * kB + tx] = f ? lr * kB + tx : -1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        const int lr = ty * kRowsPerThread + k;
+        const int i = lr * kB + tx;
+        if (!F[i]) continue;
+        if (tx > 0 && F[i - 1]) union_s(P, i, i - 1);
+        if (lr > 0) {
+            if (F[i - kB]) union_s(P, i, i - kB);
+            if (CONN == 8) {
+                if (tx > 0 && F[i - kB - 1]) union_s(P, i, i - kB - 1);
+                if (tx < kB - 1 && F[i - kB + 1]) union_s(P, i, i - kB + 1);
+            }
+        }
+    }
+    __syncthreads();
+    int roots[kRowsPerThread];
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        const int i = (ty * kRowsPerThread + k) * kB + tx;
+        roots[k] = F[i] ? find_s(P, i) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        const int lr = ty * kRowsPerThread + k;
+        const int r = r0 + lr, c = c0 + tx;
+        if (r >= a.H || c >= a.W) continue;
+        const int64_t p = (int64_t)r * a.W + c;
+        int32_t g = -1;
+        if (roots[k] >= 0) {
+            g = (int32_t)((int64_t)(r0 + roots[k] / kB) * a.W + (c0 + roots[k] % kB));
+            if (zero_acc && roots[k] == lr * kB + tx) a.A[p] = 0;
+        }
+        a.U[p] = g;
+    }
+}
+
+// 2. merges across block edges: one thread per (block, edge position):
+// positions 0..31 the top row, 32..63 the left column, 64..95 the right
+// column.
+template <int CONN>
+__global__ void uf_border_kernel(UfArgs a, int source)
+{
+    const int nbx = (int)ceil_div(a.W, kB);
+    const int64_t nblk = (int64_t)nbx * ceil_div(a.H, kB);
+    const int64_t total = nblk * 96;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t blk = t / 96;
+        const int pos = (int)(t % 96);
+        const int r0 = (int)(blk / nbx) * kB, c0 = (int)(blk % nbx) * kB;
+        int r, c;
+        if (pos < 32) {
+            r = r0; c = c0 + pos;
+            if (r == 0) continue;
+        } else if (pos < 64) {
+            r = r0 + pos - 32; c = c0;
+            if (c == 0) continue;
+        } else {
+            if (CONN != 8) continue;
+            r = r0 + pos - 64; c = c0 + kB - 1;
+            if (pos == 64 || c + 1 >= a.W) continue;   // (r0, c0+31) is handled as a top-row pixel
+        }
+        if (r >= a.H || c >= a.W) continue;
+        if (!is_fg(a.in, a.ld_in, r, c, source)) continue;
+        const int32_t p = (int32_t)((int64_t)r * a.W + c);
+        if (pos < 32) {
+            if (is_fg(a.in, a.ld_in, r - 1, c, source)) union_g(a.U, p, p - a.W);
+            if (CONN == 8) {
+                if (c > 0 && is_fg(a.in, a.ld_in, r - 1, c - 1, source)) union_g(a.U, p, p - a.W - 1);
+                if (c + 1 < a.W && is_fg(a.in, a.ld_in, r - 1, c + 1, source)) union_g(a.U, p, p - a.W + 1);
+            }
+        } else if (pos < 64) {
+            if (is_fg(a.in, a.ld_in, r, c - 1, source)) union_g(a.U, p, p - 1);
+            if (CONN == 8 && r > r0 && is_fg(a.in, a.ld_in, r - 1, c - 1, source)) union_g(a.U, p, p - a.W - 1);
+        } else {
+            if (is_fg(a.in, a.ld_in, r - 1, c + 1, source)) union_g(a.U, p, p - a.W + 1);
+        }
+    }
+}
+
+// 3. flatten: U[p] = root(p); accumulate area (warp-aggregated) or the
+// border flag at the root.
+__global__ void uf_flatten_kernel(UfArgs a, bool count_area, bool flag_border)
+{
+    const int r = blockIdx.y;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c - (int)threadIdx.x < a.W; c += gridDim.x * blockDim.x) {
+        const bool in = c < a.W;
+        const int64_t p = (int64_t)r * a.W + c;
+        int32_t root = -1;
+        if (in) {
+            const int32_t u = a.U[p];
+            if (u >= 0) {
+                root = find_g(a.U, u);
+                if (root != u) a.U[p] = root;
+            }
+        }
+        if (count_area) {
+            const unsigned act = __ballot_sync(0xffffffffu, root >= 0);
+            if (root >= 0) {
+                const unsigned peers = __match_any_sync(act, root);
+                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.A + root, __popc(peers));
+            }
+        }
+        if (flag_border && root >= 0 && (r == 0 || r == a.H - 1 || c == 0 || c == a.W - 1)) a.A[root] = 1;
+    }
+}
+
+cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, bool flag_border, cudaStream_t s)
+{
+    const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
+    const bool zero = count_area || flag_border;
+    if (conn == 8) uf_local_kernel<8><<<grid_blk, 256, 0, s>>>(a, source, zero);
+    else uf_local_kernel<4><<<grid_blk, 256, 0, s>>>(a, source, zero);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)grid_blk.x * grid_blk.y * 96;
+    int64_t nb = ceil_div(total, 256);
+    if (nb > 65535) nb = 65535;
+    if (conn == 8) uf_border_kernel<8><<<(unsigned)nb, 256, 0, s>>>(a, source);
+    else uf_border_kernel<4><<<(unsigned)nb, 256, 0, s>>>(a, source);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int bx = (int)ceil_div(a.W, 256);
+    uf_flatten_kernel<<<dim3((unsigned)bx, (unsigned)a.H), 256, 0, s>>>(a, count_area, flag_border);
+    return cudaGetLastError();
+}
+
+// 4a. labels with the area filter
+__global__ void uf_labels_kernel(UfArgs a, int32_t *labels, int64_t ld_lab, int32_t amin, int32_t amax,
+                                 int32_t *n_kept)
+{
+    const int r = blockIdx.y;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.W; c += gridDim.x * blockDim.x) {
+        const int64_t p = (int64_t)r * a.W + c;
+        const int32_t root = a.U[p];
+        int32_t out = -1;
+        if (root >= 0) {
+            const int32_t area = a.A[root];
+            if (area >= amin && area <= amax) {
+                out = root;
+                if (root == p && n_kept) atomicAdd(n_kept, 1);
+            }
+        }
+        labels[(int64_t)r * ld_lab + c] = out;
+    }
+}
+
+cudaError_t uf_labels_out(const UfArgs &a, int32_t *labels, int64_t ld_lab, int32_t min_area,
+                          int32_t max_area, int32_t *n_kept, cudaStream_t s)
+{
+    const int bx = (int)ceil_div(a.W, 256);
+    uf_labels_kernel<<<dim3((unsigned)bx, (unsigned)a.H), 256, 0, s>>>(a, labels, ld_lab, min_area, max_area,
+                                                                       n_kept);
+    return cudaGetLastError();
+}
+
+// 4b. hole filling from the background components
+__global__ void uf_fill_kernel(UfArgs a, uint8_t *out, int64_t ld_out)
+{
+    const int r = blockIdx.y;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.W; c += gridDim.x * blockDim.x) {
+        const int64_t p = (int64_t)r * a.W + c;
+        const int32_t root = a.U[p];     // background pixels have a root
+        const uint8_t v = (root < 0) ? 1 : (a.A[root] ? 0 : 1);
+        out[(int64_t)r * ld_out + c] = v;
+    }
+}
+
+cudaError_t uf_fill_out(const UfArgs &a, uint8_t *out, int64_t ld_out, cudaStream_t s)
+{
+    const int bx = (int)ceil_div(a.W, 256);
+    uf_fill_kernel<<<dim3((unsigned)bx, (unsigned)a.H), 256, 0, s>>>(a, out, ld_out);
+    return cudaGetLastError();
+}
+
+}  // namespace rtk

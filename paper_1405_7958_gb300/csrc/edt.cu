@@ -1,0 +1,148 @@
+// Exact squared Euclidean distance transform (input of the Pre-Watershed
+// step, Section 5.1):
+//     d2(p) = min over background q of (r_p - r_q)^2 + (c_p - c_q)^2.
+// Separable form (the same decomposition as Meijster et al. 2000):
+//     g(r, c)  = distance from (r, c) to the nearest background pixel of
+//                column c (vertical pass),
+//     d2(r, c) = min over c' of (c - c')^2 + g(r, c')^2 (horizontal pass).
+// Vertical pass: columns are cut into 32-row segments; a first kernel
+// records each segment's first and last background row, a second one walks
+// every segment with the carries from the segments above and below.
+// Horizontal pass: a CTA per row stages g in shared memory. For pixel c the
+// candidate c' = c gives g(r,c)^2, and any c' with |c - c'| >= sqrt(best)
+// cannot win, so the search runs outward from c and stops as soon as
+// (c - c')^2 reaches the best value found. The result is exact for any
+// input; the work per pixel grows with its distance, which is small on
+// nuclei masks.
+#include "edt.cuh"
+
+namespace rtk {
+
+constexpr int kSeg = 32;
+constexpr uint16_t kInf = 0xFFFFu;
+
+size_t edt_workspace_bytes(int H, int W)
+{
+    const int64_t nseg = ceil_div(H, kSeg);
+    return (size_t)H * W * sizeof(uint16_t) + (size_t)2 * nseg * W * sizeof(int32_t) + 256;
+}
+
+__device__ __forceinline__ bool edt_is_bg(const EdtArgs &a, int r, int c)
+{
+    if (a.lab32) return a.lab32[(int64_t)r * a.ld_in + c] < 0;
+    return a.fg8[(int64_t)r * a.ld_in + c] == 0;
+}
+
+// thread per (column, segment): first / last background row in the segment
+__global__ void edt_seg_kernel(EdtArgs a)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (c >= a.W) return;
+    const int nseg = (int)ceil_div(a.H, kSeg);
+    const int rb = s * kSeg, re = min(a.H, rb + kSeg);
+    int first = -1, last = -1;
+    for (int r = rb; r < re; ++r) {
+        if (edt_is_bg(a, r, c)) {
+            if (first < 0) first = r;
+            last = r;
+        }
+    }
+    a.seg[(int64_t)s * a.W + c] = first;
+    a.seg[(int64_t)(nseg + s) * a.W + c] = last;
+    if (first >= 0 && *a.any_bg == 0) atomicOr(a.any_bg, 1u);
+}
+
+// thread per (column, segment): g for the rows of the segment
+__global__ void edt_col_kernel(EdtArgs a)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (c >= a.W) return;
+    const int nseg = (int)ceil_div(a.H, kSeg);
+    const int rb = s * kSeg, re = min(a.H, rb + kSeg);
+    int above = -1;                      // last background row < rb
+    for (int t = s - 1; t >= 0; --t) {
+        const int v = a.seg[(int64_t)(nseg + t) * a.W + c];
+        if (v >= 0) { above = v; break; }
+    }
+    int below = -1;                      // first background row >= re
+    for (int t = s + 1; t < nseg; ++t) {
+        const int v = a.seg[(int64_t)t * a.W + c];
+        if (v >= 0) { below = v; break; }
+    }
+    int up[kSeg];
+    int last = above;
+    for (int r = rb; r < re; ++r) {
+        if (edt_is_bg(a, r, c)) last = r;
+        up[r - rb] = last;
+    }
+    int next = below;
+    for (int r = re - 1; r >= rb; --r) {
+        if (up[r - rb] == r) next = r;
+        int d = 0x7fffffff;
+        if (up[r - rb] >= 0) d = r - up[r - rb];
+        if (next >= 0 && next - r < d) d = next - r;
+        a.g[(int64_t)r * a.W + c] = d == 0x7fffffff ? kInf : (uint16_t)d;
+    }
+}
+
+// CTA per row: exact minimum over columns with early termination
+__global__ void edt_row_kernel(EdtArgs a)
+{
+    extern __shared__ uint16_t sg[];
+    const int r = blockIdx.x;
+    const uint16_t *grow = a.g + (int64_t)r * a.W;
+    for (int c = threadIdx.x; c < a.W; c += blockDim.x) sg[c] = grow[c];
+    __syncthreads();
+    const bool any = *a.any_bg != 0;
+    int32_t *out = a.d2 + (int64_t)r * a.ld_d2;
+    for (int c = threadIdx.x; c < a.W; c += blockDim.x) {
+        if (!any) {
+            out[c] = -1;
+            continue;
+        }
+        const int gc = sg[c];
+        long long best = gc == kInf ? 0x7fffffffffffLL : (long long)gc * gc;
+        for (int d = 1; (long long)d * d < best; ++d) {
+            const int cl = c - d, cr = c + d;
+            if (cl < 0 && cr >= a.W) break;
+            if (cl >= 0) {
+                const int g = sg[cl];
+                if (g != kInf) {
+                    const long long v = (long long)d * d + (long long)g * g;
+                    if (v < best) best = v;
+                }
+            }
+            if (cr < a.W) {
+                const int g = sg[cr];
+                if (g != kInf) {
+                    const long long v = (long long)d * d + (long long)g * g;
+                    if (v < best) best = v;
+                }
+            }
+        }
+        out[c] = (int32_t)best;
+    }
+}
+
+cudaError_t launch_edt(const EdtArgs &a, cudaStream_t s)
+{
+    const int nseg = (int)ceil_div(a.H, kSeg);
+    cudaError_t e = cudaMemsetAsync(a.any_bg, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const dim3 g1((unsigned)ceil_div(a.W, 128), (unsigned)nseg);
+    edt_seg_kernel<<<g1, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    edt_col_kernel<<<g1, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = (size_t)a.W * sizeof(uint16_t);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(edt_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    edt_row_kernel<<<(unsigned)a.H, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace rtk

@@ -1,0 +1,25 @@
+// Exact squared Euclidean distance transform on the GPU.
+#pragma once
+
+#include "common.cuh"
+
+namespace rtk {
+
+// Foreground source: a binary byte image (fg = byte != 0) or a label image
+// (fg = label >= 0).
+struct EdtArgs {
+    const uint8_t *fg8;     // one of fg8 / lab32 is set
+    const int32_t *lab32;
+    int64_t ld_in;
+    int H, W;
+    int32_t *d2;            // output
+    int64_t ld_d2;
+    uint16_t *g;            // workspace: vertical distance, H x W (stride W)
+    int32_t *seg;           // workspace: 2 x nseg x W (first / last background row per segment)
+    uint32_t *any_bg;       // workspace word
+};
+
+size_t edt_workspace_bytes(int H, int W);
+cudaError_t launch_edt(const EdtArgs &a, cudaStream_t s);
+
+}  // namespace rtk

@@ -1,0 +1,62 @@
+// Reconstruction by dilation on the GPU: data structures shared by the
+// kernels (recon.cu) and the host entry points (api.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace rtk {
+
+constexpr int kRTW = 128;     // tile width in pixels: 32 lanes x 4 packed bytes
+constexpr int kRStride = 33;  // shared-memory row stride in 32-bit words
+
+// One image of a reconstruction batch. The kernels work on padded copies
+// (Iw = mask, Rw = running reconstruction) of Hp x Wp pixels with row
+// stride Wp; padding holds 0 in both, which never changes and is neutral
+// for the maximum, so every tile is full-sized.
+struct ReconImage {
+    const uint8_t *marker;  // NULL: derived from the mask with h_offset
+    int64_t ld_marker;
+    const uint8_t *mask;
+    int64_t ld_mask;
+    uint8_t *Rw;
+    uint8_t *Iw;
+    int H, W, Hp, Wp;
+    int tiles_x, tiles_y;
+    int tile_base;          // index of this image's first tile in the batch
+    int h_offset;
+};
+
+constexpr int kMaxImgs = 32;
+
+// Up to kMaxImgs images, passed by value as a kernel parameter.
+struct ReconBatch {
+    int n;
+    int ntiles;
+    int64_t max_words;        // largest Hp * Wp / 4 over the images
+    ReconImage img[kMaxImgs];
+};
+
+struct SweepParams {
+    ReconBatch b;
+    int ntiles;
+    uint8_t *active;          // 2 x ntiles flags (round parity)
+    uint32_t *counters;       // 3 rotating change counters
+    uint32_t *bar;            // grid barrier state (2 words)
+    int32_t *err;             // device status word
+    int32_t *rounds_out;      // number of rounds run (statistics)
+    int max_rounds;
+    uint64_t timeout_ns;
+};
+
+int sweep_tile_rows();
+size_t sweep_smem_bytes();
+void plan_recon_image(ReconImage &d, int H, int W);
+cudaError_t launch_marker(const uint8_t *mask, int64_t ld_mask, uint8_t *marker, int64_t ld_marker, int H,
+                          int W, int h_offset, cudaStream_t s);
+cudaError_t launch_recon_init(const ReconBatch &b, int32_t *err, cudaStream_t s);
+cudaError_t launch_recon_sweep(const SweepParams &p, int conn, int num_sms, cudaStream_t s,
+                               int *grid_used);
+cudaError_t launch_recon_out(const uint8_t *Rw, int Wp, uint8_t *out, int64_t ld_out, int H, int W,
+                             uint8_t *bin, int64_t ld_bin, int threshold, cudaStream_t s);
+
+}  // namespace rtk
