@@ -65,7 +65,7 @@ typedef enum {
 /* Propagation variants of rt_reconstruct; all give identical output. */
 enum {
     RT_AUTO = 0,    /* library choice */
-    RT_RASTER = 1,  /* tile-resident directional sweeps, active-tile rounds */
+    RT_RASTER = 1,  /* tile-resident directional sweeps over flagged tiles */
     RT_QUEUE = 2,   /* pixel frontier queue (irregular wavefront propagation) */
     RT_HYBRID = 3   /* sweeps while the frontier is large, then the queue */
 };
@@ -179,13 +179,13 @@ enum {
  * ms[phase] and its number of bracketed intervals to count[phase] (arrays of
  * RT_NPHASES, either may be NULL), and forgets the records if reset != 0.
  * rt_kernel_launches returns how many kernels the context has launched.
- * rt_last_rounds waits for the device and returns the number of propagation
- * rounds of the last reconstruction (statistics; 0 if none).
+ * rt_last_visits waits for the device and returns how many tile visits the
+ * last reconstruction made (statistics; 0 if none).
  */
 RT_API rt_status rt_timing_enable(rt_ctx *ctx, int enable);
 RT_API rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset);
 RT_API int64_t rt_kernel_launches(const rt_ctx *ctx);
-RT_API int rt_last_rounds(rt_ctx *ctx);
+RT_API int64_t rt_last_visits(rt_ctx *ctx);
 
 /* One tile of a batch. Every pointer is a device pointer. */
 typedef struct {
@@ -213,7 +213,7 @@ typedef struct {
     int conn_recon;  /* connectivity of the reconstruction (8) */
     int conn_fill;   /* connectivity of the background flood in fill-holes (4) */
     int variant;     /* reconstruction variant for every tile (RT_AUTO) */
-    int max_rounds;  /* bound on propagation rounds per tile; 0 = default */
+    int max_local;   /* local sweep iterations per tile visit; 0 = default (8) */
 } rt_seg_params;
 
 /* Fill `p` with the defaults listed above. */

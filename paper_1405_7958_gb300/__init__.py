@@ -96,8 +96,8 @@ class Context:
     def kernel_launches(self) -> int:
         return lib().rt_kernel_launches(self._h)
 
-    def last_rounds(self) -> int:
-        return lib().rt_last_rounds(self._h)
+    def last_visits(self) -> int:
+        return lib().rt_last_visits(self._h)
 
     def close(self):
         if self._h:
@@ -193,7 +193,7 @@ class SegParams:
     conn_recon: int = 8
     conn_fill: int = 4
     variant: int = RT_AUTO
-    max_rounds: int = 0
+    max_local: int = 0
 
     def to_c(self) -> _native.RtSegParams:
         p = _native.RtSegParams()

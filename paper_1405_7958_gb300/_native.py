@@ -17,7 +17,7 @@ RT_AUTO, RT_RASTER, RT_QUEUE, RT_HYBRID = range(4)
 EXPORTS = (
     "rt_create", "rt_destroy", "rt_status_str", "rt_version", "rt_workspace_bytes", "rt_marker",
     "rt_reconstruct", "rt_fill_holes", "rt_label_area", "rt_edt", "rt_seg_params_default",
-    "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_last_rounds",
+    "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_last_visits",
 )
 RT_NPHASES = 6
 PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt")
@@ -41,7 +41,7 @@ class RtTile(ctypes.Structure):
 
 class RtSegParams(ctypes.Structure):
     _fields_ = [(n, _int) for n in ("h_offset", "threshold", "min_area", "max_area", "conn_recon",
-                                    "conn_fill", "variant", "max_rounds")]
+                                    "conn_fill", "variant", "max_local")]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -78,6 +78,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_timing_read.restype = _int
     lib.rt_kernel_launches.argtypes = [_vp]
     lib.rt_kernel_launches.restype = _i64
-    lib.rt_last_rounds.argtypes = [_vp]
-    lib.rt_last_rounds.restype = _int
+    lib.rt_last_visits.argtypes = [_vp]
+    lib.rt_last_visits.restype = _i64
     return lib

@@ -23,7 +23,7 @@ struct rt_ctx {
     int num_sms = 0;
     void *ws = nullptr;       // device workspace
     size_t ws_bytes = 0;
-    int32_t *rounds_dev = nullptr;   // rounds of the last reconstruction (in the workspace)
+    uint32_t *visits_dev = nullptr;  // tile visits of the last reconstruction (in the workspace)
     int64_t launches = 0;     // kernels launched
     bool timing = false;
     std::vector<PhaseRec> recs;
@@ -68,7 +68,7 @@ class Phase {
     PhaseRec rec_{0, nullptr, nullptr};
 };
 
-constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;   // 2 s per barrier wait
+constexpr uint64_t kSweepTimeoutNs = 20000000000ull;   // 20 s bound on one propagation
 
 // Bump allocator over the context workspace (256-byte aligned pieces).
 struct Carve {
@@ -108,7 +108,7 @@ rt_status ensure_ws(rt_ctx *ctx, size_t bytes)
         cudaFree(ctx->ws);
         ctx->ws = nullptr;
         ctx->ws_bytes = 0;
-        ctx->rounds_dev = nullptr;
+        ctx->visits_dev = nullptr;
     }
     size_t want = (size_t)round_up((int64_t)bytes, 1 << 20);
     if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
@@ -139,19 +139,17 @@ rt_status cuda_status(cudaError_t e)
 
 // ---------------------------------------------------------------- recon
 struct ReconWs {
-    uint8_t *active;
-    uint32_t *ctl;     // counters[3], bar[2]
+    uint32_t *flags;   // per tile
+    uint32_t *ctl;     // [0] pending, [1] visits
     int32_t *err;
-    int32_t *rounds;
 };
 
 // Reserve the sweep control block and per-image padded buffers.
 void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w)
 {
-    w.active = cv.take<uint8_t>((size_t)2 * b.ntiles);
+    w.flags = cv.take<uint32_t>((size_t)b.ntiles);
     w.ctl = cv.take<uint32_t>(8);
     w.err = cv.take<int32_t>(1);
-    w.rounds = cv.take<int32_t>(1);
     for (int i = 0; i < b.n; ++i) {
         ReconImage &d = b.img[i];
         d.Rw = cv.take<uint8_t>((size_t)d.Hp * d.Wp);
@@ -161,29 +159,26 @@ void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w)
 
 // Enqueue init + sweeps for a batch whose buffers are carved. `err` receives
 // the device status.
-rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int max_rounds, int32_t *err,
+rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int max_local, int32_t *err,
                     cudaStream_t s)
 {
-    // round 0 visits every tile; flags of round 1 start clear
-    RT_CUDA_TRY(cudaMemsetAsync(w.active, 1, (size_t)b.ntiles, s));
-    RT_CUDA_TRY(cudaMemsetAsync(w.active + b.ntiles, 0, (size_t)b.ntiles, s));
+    // every tile starts flagged (set by the init kernel with `pending`)
     RT_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, 8 * sizeof(uint32_t), s));
     {
         Phase ph(ctx, RT_PHASE_RECON_INIT, s);
-        RT_CUDA_TRY(launch_recon_init(b, err, s));
+        RT_CUDA_TRY(launch_recon_init(b, w.flags, w.ctl, err, s));
         ctx->launches += 1;
     }
-    ctx->rounds_dev = w.rounds;
+    ctx->visits_dev = w.ctl + 1;
     SweepParams p;
     p.b = b;
     p.ntiles = b.ntiles;
-    p.active = w.active;
-    p.counters = w.ctl;
-    p.bar = w.ctl + 4;
+    p.flags = w.flags;
+    p.pending = w.ctl;
     p.err = err;
-    p.rounds_out = w.rounds;
-    p.max_rounds = max_rounds > 0 ? max_rounds : 1 << 20;
-    p.timeout_ns = kBarrierTimeoutNs;
+    p.visits = w.ctl + 1;
+    p.max_local = max_local > 0 ? max_local : 8;
+    p.timeout_ns = kSweepTimeoutNs;
     int grid = 0;
     Phase ph(ctx, RT_PHASE_RECON_SWEEP, s);
     ctx->launches += 1;
@@ -312,12 +307,12 @@ rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset)
 
 int64_t rt_kernel_launches(const rt_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
-int rt_last_rounds(rt_ctx *ctx)
+int64_t rt_last_visits(rt_ctx *ctx)
 {
-    if (!ctx || !ctx->rounds_dev) return 0;
+    if (!ctx || !ctx->visits_dev) return 0;
     DeviceGuard g(ctx->device);
-    int32_t v = 0;
-    if (cudaMemcpy(&v, ctx->rounds_dev, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    uint32_t v = 0;
+    if (cudaMemcpy(&v, ctx->visits_dev, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -479,7 +474,7 @@ void rt_seg_params_default(rt_seg_params *p)
     p->conn_recon = 8;
     p->conn_fill = 4;
     p->variant = RT_AUTO;
-    p->max_rounds = 0;
+    p->max_local = 0;
 }
 
 rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_seg_params *params, void *stream)
@@ -543,7 +538,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         layout(cv, w, Bs, Fw, U, A, edt_ws);
 
         RT_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
-        st = run_recon(ctx, b, w, P.conn_recon, P.max_rounds, w.err, s);
+        st = run_recon(ctx, b, w, P.conn_recon, P.max_local, w.err, s);
         if (st != RT_OK) return st;
         for (int i = 0; i < cn; ++i) {
             const rt_tile &t = tiles[c0 + i];

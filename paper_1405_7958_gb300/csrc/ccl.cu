@@ -27,11 +27,14 @@ __device__ __forceinline__ bool is_fg(const uint8_t *in, int64_t ld, int r, int 
 }
 
 // --------------------------------------------------- shared-memory forest
+// Path halving on a shared-memory forest (same ancestor argument as below).
 __device__ __forceinline__ int find_s(volatile int *P, int x)
 {
     int p = P[x];
     while (p != x) {
-        x = p;
+        const int gp = P[p];
+        if (gp != p) P[x] = gp;
+        x = gp;
         p = P[x];
     }
     return x;
@@ -55,11 +58,17 @@ __device__ __forceinline__ void union_s(int *P, int a, int b)
 }
 
 // ---------------------------------------------------- global forest
-__device__ __forceinline__ int32_t find_g(const int32_t *U, int32_t x)
+__device__ __forceinline__ int32_t find_g(int32_t *U, int32_t x)
 {
+    // path halving: every visited node is pointed at its grandparent. A
+    // stored value is always an ancestor of the node (parents only move to
+    // smaller indices in the same tree), so concurrent finds and unions stay
+    // consistent.
     int32_t p = ld_relaxed_i32(U + x);
     while (p != x) {
-        x = p;
+        const int32_t gp = ld_relaxed_i32(U + p);
+        if (gp != p) U[x] = gp;
+        x = gp;
         p = ld_relaxed_i32(U + x);
     }
     return x;
@@ -80,101 +89,113 @@ __device__ __forceinline__ void union_g(int32_t *U, int32_t a, int32_t b)
     }
 }
 
-// 1. block-local forests. Block of 32 x 32 pixels, 256 threads: thread
-// (tx, ty) owns column tx, rows 4*ty .. 4*ty+3.
+// 1. block-local forests. Block of 32 x 32 pixels, 8 warps; warp w owns rows
+// 4w .. 4w+3 and lane = column. Inside a row, a run of foreground pixels
+// is one tree from the start: every pixel points at the run's first pixel
+// (found from the row's ballot mask). Rows are then joined with one union per
+// pair of touching runs: for 4-connectivity at the first column where the
+// runs overlap; for 8-connectivity the first pixel of a run joins each run of
+// the row above that starts within its three upper neighbours, and any other
+// pixel joins only a run of the row above that starts at its upper-right
+// neighbour.
 template <int CONN>
 __global__ void __launch_bounds__(256) uf_local_kernel(UfArgs a, int source, bool zero_acc)
 {
     __shared__ int P[kB * kB];
-    __shared__ uint8_t F[kB * kB];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    __shared__ uint32_t M[kB];
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
+    const int c = c0 + tx;
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
-        const int lr = ty * kRowsPerThread + k;
-        const int r = r0 + lr, c = c0 + tx;
+        const int lr = w * kRowsPerThread + k;
+        const int r = r0 + lr;
         const bool f = (r < a.H && c < a.W) && is_fg(a.in, a.ld_in, r, c, source);
-        F[lr * kB + tx] = f;
-        P[lr * kB + tx] = f ? lr * kB + tx : -1;
+        const uint32_t m = __ballot_sync(0xffffffffu, f);
+        const uint32_t starts = m & ~(m << 1);
+        if (tx == 0) M[lr] = m;
+        int v = -1;
+        if (f) v = lr * kB + (31 - __clz(starts & (0xffffffffu >> (31 - tx))));
+        P[lr * kB + tx] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
-        const int lr = ty * kRowsPerThread + k;
+        const int lr = w * kRowsPerThread + k;
+        if (lr == 0) continue;
+        const uint32_t m = M[lr], up = M[lr - 1];
+        if (!((m >> tx) & 1u)) continue;
         const int i = lr * kB + tx;
-        if (!F[i]) continue;
-        if (tx > 0 && F[i - 1]) union_s(P, i, i - 1);
-        if (lr > 0) {
-            if (F[i - kB]) union_s(P, i, i - kB);
-            if (CONN == 8) {
-                if (tx > 0 && F[i - kB - 1]) union_s(P, i, i - kB - 1);
-                if (tx < kB - 1 && F[i - kB + 1]) union_s(P, i, i - kB + 1);
+        const bool fl = tx > 0 && ((m >> (tx - 1)) & 1u);
+        const bool uc = (up >> tx) & 1u;
+        const bool ul = tx > 0 && ((up >> (tx - 1)) & 1u);
+        if (CONN == 4) {
+            if (uc && !(fl && ul)) union_s(P, i, i - kB);
+        } else {
+            const bool ur = tx < kB - 1 && ((up >> (tx + 1)) & 1u);
+            if (!fl) {
+                if (ul) union_s(P, i, i - kB - 1);
+                if (uc && !ul) union_s(P, i, i - kB);
+                if (ur && !uc) union_s(P, i, i - kB + 1);
+            } else if (ur && !uc) {
+                union_s(P, i, i - kB + 1);
             }
         }
     }
     __syncthreads();
-    int roots[kRowsPerThread];
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
-        const int i = (ty * kRowsPerThread + k) * kB + tx;
-        roots[k] = F[i] ? find_s(P, i) : -1;
-    }
-#pragma unroll
-    for (int k = 0; k < kRowsPerThread; ++k) {
-        const int lr = ty * kRowsPerThread + k;
-        const int r = r0 + lr, c = c0 + tx;
+        const int lr = w * kRowsPerThread + k;
+        const int r = r0 + lr;
+        const int i = lr * kB + tx;
+        const int root = P[i] >= 0 ? find_s(P, i) : -1;
         if (r >= a.H || c >= a.W) continue;
         const int64_t p = (int64_t)r * a.W + c;
         int32_t g = -1;
-        if (roots[k] >= 0) {
-            g = (int32_t)((int64_t)(r0 + roots[k] / kB) * a.W + (c0 + roots[k] % kB));
-            if (zero_acc && roots[k] == lr * kB + tx) a.A[p] = 0;
+        if (root >= 0) {
+            g = (int32_t)((int64_t)(r0 + root / kB) * a.W + (c0 + root % kB));
+            if (zero_acc && root == i) a.A[p] = 0;
         }
         a.U[p] = g;
     }
 }
 
-// 2. merges across block edges: one thread per (block, edge position):
-// positions 0..31 the top row, 32..63 the left column, 64..95 the right
-// column.
+// 2. merges across block edges, one CTA of 96 threads per block: threads
+// 0..31 the top row (with the row above), 32..63 the left column (with the
+// column to the left), 64..95 the right column (up-right neighbours, 8 only).
+// Pixels adjacent along the same block row or column are already in one
+// block-local tree, so along an edge only the first pixel pair of each pair
+// of touching runs needs a union; the others are skipped.
 template <int CONN>
-__global__ void uf_border_kernel(UfArgs a, int source)
+__global__ void __launch_bounds__(96) uf_border_kernel(UfArgs a, int source)
 {
-    const int nbx = (int)ceil_div(a.W, kB);
-    const int64_t nblk = (int64_t)nbx * ceil_div(a.H, kB);
-    const int64_t total = nblk * 96;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t blk = t / 96;
-        const int pos = (int)(t % 96);
-        const int r0 = (int)(blk / nbx) * kB, c0 = (int)(blk % nbx) * kB;
-        int r, c;
-        if (pos < 32) {
-            r = r0; c = c0 + pos;
-            if (r == 0) continue;
-        } else if (pos < 64) {
-            r = r0 + pos - 32; c = c0;
-            if (c == 0) continue;
-        } else {
-            if (CONN != 8) continue;
-            r = r0 + pos - 64; c = c0 + kB - 1;
-            if (pos == 64 || c + 1 >= a.W) continue;   // (r0, c0+31) is handled as a top-row pixel
-        }
-        if (r >= a.H || c >= a.W) continue;
-        if (!is_fg(a.in, a.ld_in, r, c, source)) continue;
+    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
+    const int pos = threadIdx.x;
+    auto fg = [&](int r, int c) { return r >= 0 && c >= 0 && r < a.H && c < a.W && is_fg(a.in, a.ld_in, r, c, source); };
+    if (pos < 32) {
+        const int r = r0, c = c0 + pos;
+        if (r == 0 || c >= a.W || !fg(r, c)) return;
         const int32_t p = (int32_t)((int64_t)r * a.W + c);
-        if (pos < 32) {
-            if (is_fg(a.in, a.ld_in, r - 1, c, source)) union_g(a.U, p, p - a.W);
-            if (CONN == 8) {
-                if (c > 0 && is_fg(a.in, a.ld_in, r - 1, c - 1, source)) union_g(a.U, p, p - a.W - 1);
-                if (c + 1 < a.W && is_fg(a.in, a.ld_in, r - 1, c + 1, source)) union_g(a.U, p, p - a.W + 1);
-            }
-        } else if (pos < 64) {
-            if (is_fg(a.in, a.ld_in, r, c - 1, source)) union_g(a.U, p, p - 1);
-            if (CONN == 8 && r > r0 && is_fg(a.in, a.ld_in, r - 1, c - 1, source)) union_g(a.U, p, p - a.W - 1);
-        } else {
-            if (is_fg(a.in, a.ld_in, r - 1, c + 1, source)) union_g(a.U, p, p - a.W + 1);
+        const bool left_in = pos > 0 && fg(r, c - 1);          // same block row
+        const bool right_in = pos < 31 && fg(r, c + 1);
+        if (fg(r - 1, c) && !(left_in && fg(r - 1, c - 1))) union_g(a.U, p, p - a.W);
+        if (CONN == 8) {
+            if (c > 0 && fg(r - 1, c - 1) && !left_in) union_g(a.U, p, p - a.W - 1);
+            if (fg(r - 1, c + 1) && !right_in) union_g(a.U, p, p - a.W + 1);
         }
+    } else if (pos < 64) {
+        const int r = r0 + pos - 32, c = c0;
+        if (c == 0 || r >= a.H || !fg(r, c)) return;
+        const int32_t p = (int32_t)((int64_t)r * a.W + c);
+        const bool up_in = r > r0 && fg(r - 1, c);              // same block column
+        if (fg(r, c - 1) && !(up_in && fg(r - 1, c - 1))) union_g(a.U, p, p - 1);
+        if (CONN == 8 && r > r0 && fg(r - 1, c - 1) && !up_in) union_g(a.U, p, p - a.W - 1);
+    } else {
+        if (CONN != 8) return;
+        const int r = r0 + pos - 64, c = c0 + kB - 1;
+        if (r == r0 || r >= a.H || c + 1 >= a.W || !fg(r, c)) return;
+        const int32_t p = (int32_t)((int64_t)r * a.W + c);
+        if (fg(r - 1, c + 1) && !fg(r - 1, c)) union_g(a.U, p, p - a.W + 1);
     }
 }
 
@@ -213,11 +234,8 @@ cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, boo
     else uf_local_kernel<4><<<grid_blk, 256, 0, s>>>(a, source, zero);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t total = (int64_t)grid_blk.x * grid_blk.y * 96;
-    int64_t nb = ceil_div(total, 256);
-    if (nb > 65535) nb = 65535;
-    if (conn == 8) uf_border_kernel<8><<<(unsigned)nb, 256, 0, s>>>(a, source);
-    else uf_border_kernel<4><<<(unsigned)nb, 256, 0, s>>>(a, source);
+    if (conn == 8) uf_border_kernel<8><<<grid_blk, 96, 0, s>>>(a, source);
+    else uf_border_kernel<4><<<grid_blk, 96, 0, s>>>(a, source);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int bx = (int)ceil_div(a.W, 256);

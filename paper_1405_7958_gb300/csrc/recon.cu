@@ -1,40 +1,41 @@
 // ReconToNuclei (Section 5.1 of the Region Templates paper): grayscale
 // morphological reconstruction by dilation,
-//     R = lim R_k,  R_0 = min(J, I),  R_{k+1} = min(delta(R_k), I),
-// computed by tile-resident directional sweeps.
+//     R = lim R_k,  R_0 = min(J, I),  R_{k+1} = min(delta(R_k), I).
 //
-// Every update has the form R(p) <- min(I(p), max(R(p), R(q))) for a
+// Every update here has the form R(p) <- min(I(p), max(R(p), R(q))) for a
 // neighbour q, so the running image never exceeds the reconstruction and
 // only grows; any schedule of such updates that stops at a fixed point of
-// the 8- (or 4-) neighbourhood ends exactly at the reconstruction. The
-// schedule here:
-//   * the image is cut into 64 x 128 tiles; one warp owns one tile and stages
-//     it in shared memory with a one-pixel halo read from the current image;
-//   * per visit the warp runs a down and an up sweep (row by row, each row
-//     taking the maximum of the three pixels above / below it) and a
-//     left-to-right and right-to-left sweep (pixel by pixel along every
-//     row), then writes the tile back;
-//   * a persistent cooperative kernel repeats rounds of visits separated by
-//     a grid barrier; a tile is visited again only when it changed or a
-//     neighbour changed the pixels of its halo, and the kernel stops after
-//     the first round without any change.
-// The paper implements this operation as an irregular wavefront propagation
-// over active elements; here the active elements are whole tiles.
+// the 8- (or 4-) neighbourhood ends exactly at the reconstruction. The paper
+// runs the operation as an irregular wavefront propagation over active
+// elements; here the active elements are 32 x 64 tiles:
+//   * a warp visits a tile by loading it into registers as packed 16-bit
+//     pairs (lane = two columns, one register per row for R and for I),
+//     with a one-pixel halo from the current image;
+//   * it sweeps the tile until nothing changes: a down and an up sweep (each
+//     row takes the maximum of itself and the neighbouring pixels of the row
+//     just done), then a left-to-right and a right-to-left sweep along every
+//     row (rows transposed through shared memory so each lane walks one row);
+//   * it writes the tile back and flags the neighbouring tiles whose halo
+//     changed. A persistent kernel keeps visiting flagged tiles until no tile
+//     is flagged or being visited; there is no grid-wide barrier.
 #include "recon.cuh"
 
 namespace rtk {
 
-constexpr int kTH = 64;                  // tile height
 constexpr int kWarpsPerCta = 4;
-constexpr int kWarpWords = (kTH + 2) * kRStride + kTH * kRStride + 2 * (kTH + 2);
+constexpr int kTS = 33;                                  // transposed row stride (words)
+constexpr int kWarpWords = 2 * kTH * kTS + 2 * (kTH + 2);
 
-int sweep_tile_rows() { return kTH; }
 size_t sweep_smem_bytes() { return sizeof(uint32_t) * kWarpWords * kWarpsPerCta; }
 
 // ---------------------------------------------------------------- init
 // Iw = mask (0 in the padding), Rw = min(J, I). One thread per 4 pixels.
-__global__ void recon_init_kernel(const ReconBatch b, int32_t *err)
+__global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t *pending, int32_t *err)
 {
+    if (blockIdx.y == 0) {
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.ntiles; t += gridDim.x * blockDim.x) flags[t] = 1u;
+        if (blockIdx.x == 0 && threadIdx.x == 0) *pending = (uint32_t)b.ntiles;
+    }
     const ReconImage &d = b.img[blockIdx.y];
     const int64_t wpr = d.Wp / 4;
     const int64_t nwords = (int64_t)d.Hp * wpr;
@@ -69,13 +70,14 @@ __global__ void recon_init_kernel(const ReconBatch b, int32_t *err)
     if (bad) raise_status(err, RT_EMARKER);
 }
 
-cudaError_t launch_recon_init(const ReconBatch &b, int32_t *err, cudaStream_t s)
+cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *pending, int32_t *err,
+                              cudaStream_t s)
 {
     const int threads = 256;
     int64_t blocks = ceil_div(b.max_words, threads);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    recon_init_kernel<<<dim3((unsigned)blocks, (unsigned)b.n), threads, 0, s>>>(b, err);
+    recon_init_kernel<<<dim3((unsigned)blocks, (unsigned)b.n), threads, 0, s>>>(b, flags, pending, err);
     return cudaGetLastError();
 }
 
@@ -84,8 +86,8 @@ void plan_recon_image(ReconImage &d, int H, int W)
     d.H = H;
     d.W = W;
     d.Hp = (int)round_up(H, kTH);
-    d.Wp = (int)round_up(W, kRTW);
-    d.tiles_x = d.Wp / kRTW;
+    d.Wp = (int)round_up(W, kTW);
+    d.tiles_x = d.Wp / kTW;
     d.tiles_y = d.Hp / kTH;
 }
 
@@ -110,219 +112,243 @@ cudaError_t launch_marker(const uint8_t *mask, int64_t ld_mask, uint8_t *marker,
 }
 
 // --------------------------------------------------------------- sweeps
-__device__ __forceinline__ uint32_t vmax4(uint32_t a, uint32_t b) { return __vmaxu4(a, b); }
-__device__ __forceinline__ uint32_t vmin4(uint32_t a, uint32_t b) { return __vminu4(a, b); }
+__device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// two bytes (low 16 bits) -> two 16-bit lanes, and back
+__device__ __forceinline__ uint32_t widen2(uint32_t v) { return __byte_perm(v, 0u, 0x4140); }
+__device__ __forceinline__ uint32_t narrow2(uint32_t w) { return __byte_perm(w, 0u, 0x4420); }
 
-// Per-warp shared-memory layout (32-bit words):
-//   sR[(kTH + 2) * kRStride]: rows 0..kTH+1 = image rows r0-1 .. r0+kTH;
-//                              word j of a row = columns c0+4j .. c0+4j+3
-//   sI[kTH * kRStride]      : mask rows r0 .. r0+kTH-1
-//   sHL[kTH + 2], sHR[kTH + 2]: halo columns c0-1 and c0+128 (low byte)
-struct WarpTile {
-    uint32_t *sR, *sI, *sHL, *sHR;
+__device__ __forceinline__ void mark_tile(uint32_t *flags, uint32_t *pending, int t)
+{
+    if (atomicExch(flags + t, 1u) == 0u) atomicAdd(pending, 1u);
+}
+
+struct WarpBuf {
+    uint32_t *sRT, *sIT;   // kTH rows x kTS words: transposed R, I (u16x2 per word)
+    uint32_t *sHL, *sHR;   // halo columns, index i <-> tile row i - 1
 };
 
-// Down (dir = +1) or up (dir = -1) sweep: each row takes the maximum of its
-// own value and the (conn = 8: three, conn = 4: one) pixels of the row just
-// processed, capped by the mask. Returns true if a pixel changed.
-template <int CONN, int DIR>
-__device__ __forceinline__ bool sweep_vertical(const WarpTile &t, int lane)
-{
-    const int first = DIR > 0 ? 0 : kTH + 1;
-    uint32_t prev = t.sR[first * kRStride + lane];
-    uint32_t prevL = 0, prevR = 0;
-    if (CONN == 8) {
-        prevL = lane == 0 ? (t.sHL[first] << 24) : t.sR[first * kRStride + lane - 1];
-        prevR = lane == 31 ? t.sHR[first] : t.sR[first * kRStride + lane + 1];
-    }
-    bool ch = false;
-#pragma unroll 4
-    for (int k = 1; k <= kTH; ++k) {
-        const int i = DIR > 0 ? k : kTH + 1 - k;
-        uint32_t up = prev;
-        if (CONN == 8) {
-            const uint32_t left = __byte_perm(prevL, prev, 0x6543);
-            const uint32_t right = __byte_perm(prev, prevR, 0x4321);
-            up = vmax4(prev, vmax4(left, right));
-        }
-        const uint32_t cur = t.sR[i * kRStride + lane];
-        const uint32_t nw = vmin4(vmax4(cur, up), t.sI[(i - 1) * kRStride + lane]);
-        if (nw != cur) {
-            t.sR[i * kRStride + lane] = nw;
-            ch = true;
-        }
-        prev = nw;
-        if (CONN == 8) {
-            prevL = __shfl_up_sync(0xffffffffu, nw, 1);
-            prevR = __shfl_down_sync(0xffffffffu, nw, 1);
-            if (lane == 0) prevL = t.sHL[i] << 24;
-            if (lane == 31) prevR = t.sHR[i];
-        }
-    }
-    return ch;
-}
-
-// Left-to-right (DIR = +1) or right-to-left (DIR = -1) sweep along every
-// row: lane = row. Inside a word the carried value is pushed through the
-// four bytes by four shift-max-min steps (byte k is exact after step k+1).
-template <int DIR>
-__device__ __forceinline__ bool sweep_horizontal(const WarpTile &t, int lane)
-{
-    bool ch = false;
-#pragma unroll 1
-    for (int g = 0; g < kTH / 32; ++g) {
-        const int i = 1 + lane + 32 * g;       // sR row
-        uint32_t x = DIR > 0 ? t.sHL[i] : t.sHR[i];
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            const int j = DIR > 0 ? k : 31 - k;
-            const uint32_t w0 = t.sR[i * kRStride + j];
-            const uint32_t iw = t.sI[(i - 1) * kRStride + j];
-            uint32_t w = w0;
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const uint32_t sh = DIR > 0 ? ((w << 8) | x) : ((w >> 8) | (x << 24));
-                w = vmin4(vmax4(w, sh), iw);
-            }
-            x = DIR > 0 ? (w >> 24) : (w & 0xffu);
-            if (w != w0) {
-                t.sR[i * kRStride + j] = w;
-                ch = true;
-            }
-        }
-    }
-    return ch;
-}
-
+// One visit of tile t by a warp. Returns after marking the tiles to visit.
 template <int CONN>
-__device__ void visit_tile(const SweepParams &p, int t, const WarpTile &wt, int lane, uint8_t *next_active,
-                           uint32_t *counter)
+__device__ __forceinline__ void visit_tile(const SweepParams &p, int t, const WarpBuf &wb, int lane)
 {
     int k = 0;
     while (k + 1 < p.b.n && t >= p.b.img[k + 1].tile_base) ++k;
     const ReconImage &d = p.b.img[k];
     const int lt = t - d.tile_base;
     const int ty = lt / d.tiles_x, tx = lt % d.tiles_x;
-    const int r0 = ty * kTH, c0 = tx * kRTW;
-    const int Wp = d.Wp, Hp = d.Hp;
+    const int r0 = ty * kTH, c0 = tx * kTW;
+    const int64_t Wp = d.Wp;
+    const uint16_t *Rg = reinterpret_cast<const uint16_t *>(d.Rw + (int64_t)r0 * Wp + c0) + lane;
+    const uint16_t *Ig = reinterpret_cast<const uint16_t *>(d.Iw + (int64_t)r0 * Wp + c0) + lane;
+    const int64_t ws = Wp / 2;   // row stride in 16-bit units
 
-    // stage rows r0-1 .. r0+kTH of R, and the mask
-#pragma unroll 4
-    for (int i = 0; i < kTH + 2; ++i) {
-        const int r = r0 - 1 + i;
-        uint32_t w = 0;
-        if (r >= 0 && r < Hp) w = __ldcg(reinterpret_cast<const uint32_t *>(d.Rw + (int64_t)r * Wp + c0) + lane);
-        wt.sR[i * kRStride + lane] = w;
+    uint32_t R[kTH], I[kTH];
+#pragma unroll
+    for (int r = 0; r < kTH; ++r) {
+        R[r] = widen2(__ldcg(Rg + r * ws));
+        I[r] = widen2(__ldg(Ig + r * ws));
+        wb.sIT[r * kTS + lane] = I[r];
     }
-#pragma unroll 4
-    for (int i = 0; i < kTH; ++i)
-        wt.sI[i * kRStride + lane] =
-            __ldg(reinterpret_cast<const uint32_t *>(d.Iw + (int64_t)(r0 + i) * Wp + c0) + lane);
+    const uint32_t topw = r0 > 0 ? widen2(__ldcg(Rg - ws)) : 0u;
+    const uint32_t botw = r0 + kTH < d.Hp ? widen2(__ldcg(Rg + kTH * ws)) : 0u;
     for (int i = lane; i < kTH + 2; i += 32) {
         const int r = r0 - 1 + i;
         uint32_t hl = 0, hr = 0;
-        if (r >= 0 && r < Hp) {
+        if (r >= 0 && r < d.Hp) {
             if (c0 > 0) hl = __ldcg(d.Rw + (int64_t)r * Wp + c0 - 1);
-            if (c0 + kRTW < Wp) hr = __ldcg(d.Rw + (int64_t)r * Wp + c0 + kRTW);
+            if (c0 + kTW < Wp) hr = __ldcg(d.Rw + (int64_t)r * Wp + c0 + kTW);
         }
-        wt.sHL[i] = hl;
-        wt.sHR[i] = hr;
+        wb.sHL[i] = hl;
+        wb.sHR[i] = hr;
     }
     __syncwarp();
-    const uint32_t top0 = wt.sR[1 * kRStride + lane];
-    const uint32_t bot0 = wt.sR[kTH * kRStride + lane];
-    uint32_t left0[kTH / 32], right0[kTH / 32];
+
+    bool converged = false;
+    for (int it = 0; it < p.max_local; ++it) {
+        bool ch = false;
+        // down sweep
+        uint32_t prev = topw;
 #pragma unroll
-    for (int g = 0; g < kTH / 32; ++g) {
-        left0[g] = wt.sR[(1 + lane + 32 * g) * kRStride + 0] & 0xffu;
-        right0[g] = wt.sR[(1 + lane + 32 * g) * kRStride + 31] >> 24;
-    }
-
-    bool ch = sweep_vertical<CONN, +1>(wt, lane);
-    __syncwarp();
-    ch |= sweep_vertical<CONN, -1>(wt, lane);
-    __syncwarp();
-    ch |= sweep_horizontal<+1>(wt, lane);
-    __syncwarp();
-    ch |= sweep_horizontal<-1>(wt, lane);
-    __syncwarp();
-
-    if (!__any_sync(0xffffffffu, ch)) return;
-
-    // write back and work out which neighbours see a changed halo
-    const uint32_t top1 = wt.sR[1 * kRStride + lane];
-    const uint32_t bot1 = wt.sR[kTH * kRStride + lane];
-#pragma unroll 4
-    for (int i = 1; i <= kTH; ++i)
-        __stcg(reinterpret_cast<uint32_t *>(d.Rw + (int64_t)(r0 + i - 1) * Wp + c0) + lane,
-               wt.sR[i * kRStride + lane]);
-    bool lch = false, rch = false;
+        for (int r = 0; r < kTH; ++r) {
+            uint32_t m = vmax2(R[r], prev);
+            if (CONN == 8) {
+                uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
+                uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
+                if (lane == 0) sl = wb.sHL[r] << 16;
+                if (lane == 31) sr = wb.sHR[r];
+                m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
+            }
+            const uint32_t nv = vmin2(m, I[r]);
+            ch |= nv != R[r];
+            R[r] = nv;
+            prev = nv;
+        }
+        // up sweep
+        prev = botw;
 #pragma unroll
-    for (int g = 0; g < kTH / 32; ++g) {
-        lch |= (wt.sR[(1 + lane + 32 * g) * kRStride + 0] & 0xffu) != left0[g];
-        rch |= (wt.sR[(1 + lane + 32 * g) * kRStride + 31] >> 24) != right0[g];
+        for (int r = kTH - 1; r >= 0; --r) {
+            uint32_t m = vmax2(R[r], prev);
+            if (CONN == 8) {
+                uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
+                uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
+                if (lane == 0) sl = wb.sHL[r + 2] << 16;
+                if (lane == 31) sr = wb.sHR[r + 2];
+                m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
+            }
+            const uint32_t nv = vmin2(m, I[r]);
+            ch |= nv != R[r];
+            R[r] = nv;
+            prev = nv;
+        }
+        // left-to-right and right-to-left along every row (lane = row)
+#pragma unroll
+        for (int r = 0; r < kTH; ++r) wb.sRT[r * kTS + lane] = R[r];
+        __syncwarp();
+        {
+            uint32_t *row = wb.sRT + lane * kTS;
+            const uint32_t *irow = wb.sIT + lane * kTS;
+            uint32_t x = wb.sHL[lane + 1];
+#pragma unroll 8
+            for (int j = 0; j < kTW / 2; ++j) {
+                const uint32_t w = row[j], iw = irow[j];
+                const uint32_t a = min(max(w & 0xffffu, x), iw & 0xffffu);
+                x = min(max(w >> 16, a), iw >> 16);
+                const uint32_t nw = a | (x << 16);
+                if (nw != w) {
+                    row[j] = nw;
+                    ch = true;
+                }
+            }
+            x = wb.sHR[lane + 1];
+#pragma unroll 8
+            for (int j = kTW / 2 - 1; j >= 0; --j) {
+                const uint32_t w = row[j], iw = irow[j];
+                const uint32_t b = min(max(w >> 16, x), iw >> 16);
+                x = min(max(w & 0xffffu, b), iw & 0xffffu);
+                const uint32_t nw = x | (b << 16);
+                if (nw != w) {
+                    row[j] = nw;
+                    ch = true;
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kTH; ++r) R[r] = wb.sRT[r * kTS + lane];
+        __syncwarp();
+        if (!__any_sync(0xffffffffu, ch)) {
+            converged = true;
+            break;
+        }
     }
-    const bool top = __any_sync(0xffffffffu, top1 != top0);
-    const bool bot = __any_sync(0xffffffffu, bot1 != bot0);
-    const bool left = __any_sync(0xffffffffu, lch);
-    const bool right = __any_sync(0xffffffffu, rch);
-    const bool tl = __shfl_sync(0xffffffffu, (top1 ^ top0) & 0xffu, 0) != 0;
-    const bool tr = __shfl_sync(0xffffffffu, (top1 ^ top0) >> 24, 31) != 0;
-    const bool bl = __shfl_sync(0xffffffffu, (bot1 ^ bot0) & 0xffu, 0) != 0;
-    const bool br = __shfl_sync(0xffffffffu, (bot1 ^ bot0) >> 24, 31) != 0;
+
+    // write back, and find which borders moved
+    uint16_t *Rs = reinterpret_cast<uint16_t *>(d.Rw + (int64_t)r0 * Wp + c0) + lane;
+    uint32_t dl = 0, dr = 0, dtop = 0, dbot = 0, any = 0;
+#pragma unroll
+    for (int r = 0; r < kTH; ++r) {
+        const uint32_t orig = widen2(__ldcg(Rs + r * ws));
+        const uint32_t diff = orig ^ R[r];
+        if (diff) __stcg(Rs + r * ws, (uint16_t)narrow2(R[r]));
+        dl |= diff & 0xffffu;
+        dr |= diff >> 16;
+        any |= diff;
+        if (r == 0) dtop = diff;
+        if (r == kTH - 1) dbot = diff;
+    }
+    if (!__any_sync(0xffffffffu, any != 0)) return;
+    const bool top = __any_sync(0xffffffffu, dtop != 0);
+    const bool bot = __any_sync(0xffffffffu, dbot != 0);
+    const bool left = __shfl_sync(0xffffffffu, dl, 0) != 0;
+    const bool right = __shfl_sync(0xffffffffu, dr, 31) != 0;
+    const bool tl = __shfl_sync(0xffffffffu, dtop & 0xffffu, 0) != 0;
+    const bool tr = __shfl_sync(0xffffffffu, dtop >> 16, 31) != 0;
+    const bool bl = __shfl_sync(0xffffffffu, dbot & 0xffffu, 0) != 0;
+    const bool br = __shfl_sync(0xffffffffu, dbot >> 16, 31) != 0;
+    __threadfence();
     if (lane == 0) {
-        uint8_t *na = next_active + d.tile_base;
-        const int nx = d.tiles_x, ny = d.tiles_y;
-        na[lt] = 1;   // not yet at a local fixed point: visit again
-        if (top && ty > 0) na[lt - nx] = 1;
-        if (bot && ty + 1 < ny) na[lt + nx] = 1;
-        if (left && tx > 0) na[lt - 1] = 1;
-        if (right && tx + 1 < nx) na[lt + 1] = 1;
+        const int nx = d.tiles_x, ny = d.tiles_y, base = d.tile_base;
+        if (!converged) mark_tile(p.flags, p.pending, t);
+        if (top && ty > 0) mark_tile(p.flags, p.pending, base + lt - nx);
+        if (bot && ty + 1 < ny) mark_tile(p.flags, p.pending, base + lt + nx);
+        if (left && tx > 0) mark_tile(p.flags, p.pending, base + lt - 1);
+        if (right && tx + 1 < nx) mark_tile(p.flags, p.pending, base + lt + 1);
         if (CONN == 8) {
-            if (tl && ty > 0 && tx > 0) na[lt - nx - 1] = 1;
-            if (tr && ty > 0 && tx + 1 < nx) na[lt - nx + 1] = 1;
-            if (bl && ty + 1 < ny && tx > 0) na[lt + nx - 1] = 1;
-            if (br && ty + 1 < ny && tx + 1 < nx) na[lt + nx + 1] = 1;
+            if (tl && ty > 0 && tx > 0) mark_tile(p.flags, p.pending, base + lt - nx - 1);
+            if (tr && ty > 0 && tx + 1 < nx) mark_tile(p.flags, p.pending, base + lt - nx + 1);
+            if (bl && ty + 1 < ny && tx > 0) mark_tile(p.flags, p.pending, base + lt + nx - 1);
+            if (br && ty + 1 < ny && tx + 1 < nx) mark_tile(p.flags, p.pending, base + lt + nx + 1);
         }
-        atomicAdd(counter, 1u);
     }
 }
 
+// Persistent propagation. Warp w owns tiles w, w + nwarps, ...; it visits
+// those flagged, and leaves when nothing is flagged or being visited
+// anywhere. A visit is counted in `pending` from the moment its tile is
+// flagged until after the visit has flagged its neighbours, so pending = 0
+// means the image is at the fixed point. The launch is cooperative only to
+// guarantee that every warp is resident (a flagged tile's owner always runs).
 template <int CONN>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_sweep_kernel(SweepParams p)
 {
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpTile wt;
-    wt.sR = smem + warp * kWarpWords;
-    wt.sI = wt.sR + (kTH + 2) * kRStride;
-    wt.sHL = wt.sI + kTH * kRStride;
-    wt.sHR = wt.sHL + (kTH + 2);
+    WarpBuf wb;
+    wb.sRT = smem + warp * kWarpWords;
+    wb.sIT = wb.sRT + kTH * kTS;
+    wb.sHL = wb.sIT + kTH * kTS;
+    wb.sHR = wb.sHL + (kTH + 2);
     const int gw = blockIdx.x * kWarpsPerCta + warp;
     const int nw = gridDim.x * kWarpsPerCta;
-    int round = 0;
-    for (; round < p.max_rounds; ++round) {
-        uint8_t *act = p.active + (size_t)(round & 1) * p.ntiles;
-        uint8_t *nxt = p.active + (size_t)((round + 1) & 1) * p.ntiles;
-        uint32_t *cnt = p.counters + (round % 3);
+    const uint64_t t_start = globaltimer_ns();
+    uint32_t nvisits = 0;
+    int idle = 0;
+    for (;;) {
+        bool did = false;
         for (int t = gw; t < p.ntiles; t += nw) {
-            if (!__ldcg(act + t)) continue;
-            if (lane == 0) act[t] = 0;
-            visit_tile<CONN>(p, t, wt, lane, nxt, cnt);
+            uint32_t f = 0;
+            if (lane == 0) {
+                f = *reinterpret_cast<volatile uint32_t *>(p.flags + t);
+                if (f) f = atomicExch(p.flags + t, 0u);
+            }
+            if (!__shfl_sync(0xffffffffu, f, 0)) continue;
+            __threadfence();
+            visit_tile<CONN>(p, t, wb, lane);
+            if (lane == 0) atomicSub(p.pending, 1u);
+            did = true;
+            ++nvisits;
         }
-        if (!grid_barrier(p.bar, gridDim.x, p.err, p.timeout_ns)) return;
-        const uint32_t changed = ld_acquire(cnt);
-        if (blockIdx.x == 0 && threadIdx.x == 0) p.counters[(round + 2) % 3] = 0;
-        if (changed == 0) break;
+        if (did) {
+            idle = 0;
+            continue;
+        }
+        uint32_t pend = 0;
+        if (lane == 0) pend = ld_acquire(p.pending);
+        pend = __shfl_sync(0xffffffffu, pend, 0);
+        if (pend == 0) break;
+        if (++idle > 8) __nanosleep(200);
+        int late = 0;
+        if (lane == 0 && (idle & 63) == 0) late = globaltimer_ns() - t_start > p.timeout_ns;
+        if (__shfl_sync(0xffffffffu, late, 0)) {
+            if (lane == 0) raise_status(p.err, RT_ETIMEOUT);
+            break;
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (p.rounds_out) *p.rounds_out = round + 1;
-        if (round >= p.max_rounds) raise_status(p.err, RT_ETIMEOUT);
-    }
+    if (lane == 0 && p.visits && nvisits) atomicAdd(p.visits, nvisits);
 }
 
-cudaError_t launch_recon_sweep(const SweepParams &p, int conn, int num_sms, cudaStream_t s,
-                               int *grid_used)
+cudaError_t launch_recon_sweep(const SweepParams &p, int conn, int num_sms, cudaStream_t s, int *grid_used)
 {
     const size_t smem = sweep_smem_bytes();
     const void *fn = conn == 8 ? (const void *)recon_sweep_kernel<8> : (const void *)recon_sweep_kernel<4>;

@@ -6,13 +6,13 @@
 
 namespace rtk {
 
-constexpr int kRTW = 128;     // tile width in pixels: 32 lanes x 4 packed bytes
-constexpr int kRStride = 33;  // shared-memory row stride in 32-bit words
+constexpr int kTH = 32;       // warp tile: 32 rows
+constexpr int kTW = 64;       //            x 64 columns (2 per lane)
 
 // One image of a reconstruction batch. The kernels work on padded copies
-// (Iw = mask, Rw = running reconstruction) of Hp x Wp pixels with row
-// stride Wp; padding holds 0 in both, which never changes and is neutral
-// for the maximum, so every tile is full-sized.
+// (Iw = mask, Rw = running reconstruction) of Hp x Wp pixels (multiples of
+// the 32 x 64 tile) with row stride Wp; padding holds 0 in both, which never
+// changes and is neutral for the maximum, so every tile is full-sized.
 struct ReconImage {
     const uint8_t *marker;  // NULL: derived from the mask with h_offset
     int64_t ld_marker;
@@ -39,21 +39,20 @@ struct ReconBatch {
 struct SweepParams {
     ReconBatch b;
     int ntiles;
-    uint8_t *active;          // 2 x ntiles flags (round parity)
-    uint32_t *counters;       // 3 rotating change counters
-    uint32_t *bar;            // grid barrier state (2 words)
+    uint32_t *flags;          // per tile: nonzero = must be visited
+    uint32_t *pending;        // flagged + in-progress visits
     int32_t *err;             // device status word
-    int32_t *rounds_out;      // number of rounds run (statistics)
-    int max_rounds;
-    uint64_t timeout_ns;
+    uint32_t *visits;         // number of tile visits (statistics)
+    int max_local;            // local iterations per visit before revisiting
+    uint64_t timeout_ns;      // bound on the whole propagation
 };
 
-int sweep_tile_rows();
 size_t sweep_smem_bytes();
 void plan_recon_image(ReconImage &d, int H, int W);
 cudaError_t launch_marker(const uint8_t *mask, int64_t ld_mask, uint8_t *marker, int64_t ld_marker, int H,
                           int W, int h_offset, cudaStream_t s);
-cudaError_t launch_recon_init(const ReconBatch &b, int32_t *err, cudaStream_t s);
+cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *pending, int32_t *err,
+                              cudaStream_t s);
 cudaError_t launch_recon_sweep(const SweepParams &p, int conn, int num_sms, cudaStream_t s,
                                int *grid_used);
 cudaError_t launch_recon_out(const uint8_t *Rw, int Wp, uint8_t *out, int64_t ld_out, int H, int W,

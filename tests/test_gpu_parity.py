@@ -203,3 +203,13 @@ def test_chain_full_4k(rt):
     I = synth.config2_tile(2000)
     out = rt.segment_batch([dev(I)], want_recon=True, want_filled=True)[0]
     check_chain(out, I)
+
+
+def test_chain_independent_of_local_iterations(rt):
+    """Bytes do not depend on how the propagation is scheduled."""
+    I = synth.config2_tile(31, H=700, W=900)
+    a = rt.segment_batch([dev(I)], rt.SegParams(max_local=1))[0]
+    b = rt.segment_batch([dev(I)], rt.SegParams(max_local=32))[0]
+    for k in ("R", "F", "L", "D"):
+        assert np.array_equal(host(a[k]), host(b[k]))
+    check_chain(a, I)
