@@ -196,7 +196,7 @@ def run_native(a, rank, world, local_rank):
     for _ in range(a.warmup):
         outs = rt.segment_batch(imgs, params, outputs=outs, ctx=ctx)
     torch.cuda.synchronize()
-    visits = ctx.last_visits()
+    visits = ctx.recon_stats()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     ctx.timing(True)
     ctx.read_timing(reset=True)
@@ -293,7 +293,7 @@ def run_native(a, rank, world, local_rank):
             "chain_hbm_gbs": chain_bytes / (total_ms / 1000.0) / 1e9,
             "roofline": roof,
             "phases_ms_per_step": {k: v[0] / a.steps for k, v in phases.items()},
-            "recon_tile_visits_per_step": visits,
+            "recon_visits_iterations_per_step": visits,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

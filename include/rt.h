@@ -179,13 +179,14 @@ enum {
  * ms[phase] and its number of bracketed intervals to count[phase] (arrays of
  * RT_NPHASES, either may be NULL), and forgets the records if reset != 0.
  * rt_kernel_launches returns how many kernels the context has launched.
- * rt_last_visits waits for the device and returns how many tile visits the
- * last reconstruction made (statistics; 0 if none).
+ * rt_recon_stats waits for the device and reports how many tile visits and
+ * local sweep iterations the last reconstruction made (statistics; 0 if
+ * none); either pointer may be NULL.
  */
 RT_API rt_status rt_timing_enable(rt_ctx *ctx, int enable);
 RT_API rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset);
 RT_API int64_t rt_kernel_launches(const rt_ctx *ctx);
-RT_API int64_t rt_last_visits(rt_ctx *ctx);
+RT_API rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iterations);
 
 /* One tile of a batch. Every pointer is a device pointer. */
 typedef struct {

@@ -96,8 +96,11 @@ class Context:
     def kernel_launches(self) -> int:
         return lib().rt_kernel_launches(self._h)
 
-    def last_visits(self) -> int:
-        return lib().rt_last_visits(self._h)
+    def recon_stats(self) -> tuple:
+        """(tile visits, local sweep iterations) of the last reconstruction."""
+        v, it = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().rt_recon_stats(self._h, ctypes.byref(v), ctypes.byref(it)), "rt_recon_stats")
+        return v.value, it.value
 
     def close(self):
         if self._h:

@@ -17,7 +17,7 @@ RT_AUTO, RT_RASTER, RT_QUEUE, RT_HYBRID = range(4)
 EXPORTS = (
     "rt_create", "rt_destroy", "rt_status_str", "rt_version", "rt_workspace_bytes", "rt_marker",
     "rt_reconstruct", "rt_fill_holes", "rt_label_area", "rt_edt", "rt_seg_params_default",
-    "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_last_visits",
+    "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_recon_stats",
 )
 RT_NPHASES = 6
 PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt")
@@ -78,6 +78,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_timing_read.restype = _int
     lib.rt_kernel_launches.argtypes = [_vp]
     lib.rt_kernel_launches.restype = _i64
-    lib.rt_last_visits.argtypes = [_vp]
-    lib.rt_last_visits.restype = _i64
+    lib.rt_recon_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+    lib.rt_recon_stats.restype = _int
     return lib

@@ -23,7 +23,7 @@ struct rt_ctx {
     int num_sms = 0;
     void *ws = nullptr;       // device workspace
     size_t ws_bytes = 0;
-    uint32_t *visits_dev = nullptr;  // tile visits of the last reconstruction (in the workspace)
+    uint32_t *visits_dev = nullptr;  // [visits, iterations] of the last reconstruction (workspace)
     int64_t launches = 0;     // kernels launched
     bool timing = false;
     std::vector<PhaseRec> recs;
@@ -140,7 +140,7 @@ rt_status cuda_status(cudaError_t e)
 // ---------------------------------------------------------------- recon
 struct ReconWs {
     uint32_t *flags;   // per tile
-    uint32_t *ctl;     // [0] pending, [1] visits
+    uint32_t *ctl;     // [0] pending, [1] visits, [2] local iterations
     int32_t *err;
 };
 
@@ -307,16 +307,20 @@ rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset)
 
 int64_t rt_kernel_launches(const rt_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
-int64_t rt_last_visits(rt_ctx *ctx)
+rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iterations)
 {
-    if (!ctx || !ctx->visits_dev) return 0;
-    DeviceGuard g(ctx->device);
-    uint32_t v = 0;
-    if (cudaMemcpy(&v, ctx->visits_dev, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
+    if (!ctx) return RT_EINVAL;
+    uint32_t v[2] = {0, 0};
+    if (ctx->visits_dev) {
+        DeviceGuard g(ctx->device);
+        if (cudaMemcpy(v, ctx->visits_dev, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return RT_ECUDA;
+        }
     }
-    return v;
+    if (visits) *visits = v[0];
+    if (iterations) *iterations = v[1];
+    return RT_OK;
 }
 
 rt_status rt_marker(rt_ctx *ctx, const uint8_t *mask, int64_t ld_mask, uint8_t *marker, int64_t ld_marker, int H,

@@ -27,8 +27,20 @@ __device__ __forceinline__ bool is_fg(const uint8_t *in, int64_t ld, int r, int 
 }
 
 // --------------------------------------------------- shared-memory forest
-// Path halving on a shared-memory forest (same ancestor argument as below).
+// Finds that run while unions are still hooking roots only read; path
+// halving (every visited node pointed at its grandparent) is used only
+// after all unions of the forest have finished.
 __device__ __forceinline__ int find_s(volatile int *P, int x)
+{
+    int p = P[x];
+    while (p != x) {
+        x = p;
+        p = P[x];
+    }
+    return x;
+}
+
+__device__ __forceinline__ int find_s_halve(volatile int *P, int x)
 {
     int p = P[x];
     while (p != x) {
@@ -58,16 +70,27 @@ __device__ __forceinline__ void union_s(int *P, int a, int b)
 }
 
 // ---------------------------------------------------- global forest
-__device__ __forceinline__ int32_t find_g(int32_t *U, int32_t x)
+__device__ __forceinline__ int32_t find_g(const int32_t *U, int32_t x)
 {
-    // path halving: every visited node is pointed at its grandparent. A
-    // stored value is always an ancestor of the node (parents only move to
-    // smaller indices in the same tree), so concurrent finds and unions stay
-    // consistent.
+    int32_t p = ld_relaxed_i32(U + x);
+    while (p != x) {
+        x = p;
+        p = ld_relaxed_i32(U + x);
+    }
+    return x;
+}
+
+// Path halving for the flatten pass (after every union is done). Other
+// threads store final roots into the same nodes meanwhile; since every
+// ancestor has a smaller index than its descendants and the root is the
+// smallest of all, the halving store is an atomicMin, so no node can move
+// back from its root to a lower ancestor.
+__device__ __forceinline__ int32_t find_g_halve(int32_t *U, int32_t x)
+{
     int32_t p = ld_relaxed_i32(U + x);
     while (p != x) {
         const int32_t gp = ld_relaxed_i32(U + p);
-        if (gp != p) U[x] = gp;
+        if (gp != p) atomicMin(U + x, gp);
         x = gp;
         p = ld_relaxed_i32(U + x);
     }
@@ -148,7 +171,7 @@ __global__ void __launch_bounds__(256) uf_local_kernel(UfArgs a, int source, boo
         const int lr = w * kRowsPerThread + k;
         const int r = r0 + lr;
         const int i = lr * kB + tx;
-        const int root = P[i] >= 0 ? find_s(P, i) : -1;
+        const int root = P[i] >= 0 ? find_s_halve(P, i) : -1;
         if (r >= a.H || c >= a.W) continue;
         const int64_t p = (int64_t)r * a.W + c;
         int32_t g = -1;
@@ -211,8 +234,8 @@ __global__ void uf_flatten_kernel(UfArgs a, bool count_area, bool flag_border)
         if (in) {
             const int32_t u = a.U[p];
             if (u >= 0) {
-                root = find_g(a.U, u);
-                if (root != u) a.U[p] = root;
+                root = find_g_halve(a.U, u);
+                if (root != u) atomicMin(a.U + p, root);
             }
         }
         if (count_area) {

@@ -140,7 +140,7 @@ struct WarpBuf {
 
 // One visit of tile t by a warp. Returns after marking the tiles to visit.
 template <int CONN>
-__device__ __forceinline__ void visit_tile(const SweepParams &p, int t, const WarpBuf &wb, int lane)
+__device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, const WarpBuf &wb, int lane)
 {
     int k = 0;
     while (k + 1 < p.b.n && t >= p.b.img[k + 1].tile_base) ++k;
@@ -175,7 +175,8 @@ __device__ __forceinline__ void visit_tile(const SweepParams &p, int t, const Wa
     __syncwarp();
 
     bool converged = false;
-    for (int it = 0; it < p.max_local; ++it) {
+    int it = 0;
+    for (; it < p.max_local; ++it) {
         bool ch = false;
         // down sweep
         uint32_t prev = topw;
@@ -249,6 +250,7 @@ __device__ __forceinline__ void visit_tile(const SweepParams &p, int t, const Wa
         __syncwarp();
         if (!__any_sync(0xffffffffu, ch)) {
             converged = true;
+            ++it;
             break;
         }
     }
@@ -267,7 +269,7 @@ __device__ __forceinline__ void visit_tile(const SweepParams &p, int t, const Wa
         if (r == 0) dtop = diff;
         if (r == kTH - 1) dbot = diff;
     }
-    if (!__any_sync(0xffffffffu, any != 0)) return;
+    if (!__any_sync(0xffffffffu, any != 0)) return (uint32_t)it;
     const bool top = __any_sync(0xffffffffu, dtop != 0);
     const bool bot = __any_sync(0xffffffffu, dbot != 0);
     const bool left = __shfl_sync(0xffffffffu, dl, 0) != 0;
@@ -291,6 +293,7 @@ __device__ __forceinline__ void visit_tile(const SweepParams &p, int t, const Wa
             if (br && ty + 1 < ny && tx + 1 < nx) mark_tile(p.flags, p.pending, base + lt + nx + 1);
         }
     }
+    return (uint32_t)it;
 }
 
 // Persistent propagation. Warp w owns tiles w, w + nwarps, ...; it visits
@@ -312,22 +315,28 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_sweep_kernel(SweepPar
     const int gw = blockIdx.x * kWarpsPerCta + warp;
     const int nw = gridDim.x * kWarpsPerCta;
     const uint64_t t_start = globaltimer_ns();
-    uint32_t nvisits = 0;
+    uint32_t nvisits = 0, niters = 0;
     int idle = 0;
     for (;;) {
         bool did = false;
-        for (int t = gw; t < p.ntiles; t += nw) {
-            uint32_t f = 0;
-            if (lane == 0) {
-                f = *reinterpret_cast<volatile uint32_t *>(p.flags + t);
-                if (f) f = atomicExch(p.flags + t, 0u);
+        // the warp's tiles, 32 flags per load
+        for (int base = gw; base < p.ntiles; base += nw * 32) {
+            const int tl = base + lane * nw;
+            const bool f = tl < p.ntiles && *reinterpret_cast<volatile uint32_t *>(p.flags + tl) != 0u;
+            uint32_t mask = __ballot_sync(0xffffffffu, f);
+            while (mask) {
+                const int i = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int t = base + i * nw;
+                uint32_t got = 0;
+                if (lane == 0) got = atomicExch(p.flags + t, 0u);
+                if (!__shfl_sync(0xffffffffu, got, 0)) continue;
+                __threadfence();
+                niters += visit_tile<CONN>(p, t, wb, lane);
+                if (lane == 0) atomicSub(p.pending, 1u);
+                did = true;
+                ++nvisits;
             }
-            if (!__shfl_sync(0xffffffffu, f, 0)) continue;
-            __threadfence();
-            visit_tile<CONN>(p, t, wb, lane);
-            if (lane == 0) atomicSub(p.pending, 1u);
-            did = true;
-            ++nvisits;
         }
         if (did) {
             idle = 0;
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_sweep_kernel(SweepPar
         if (lane == 0) pend = ld_acquire(p.pending);
         pend = __shfl_sync(0xffffffffu, pend, 0);
         if (pend == 0) break;
-        if (++idle > 8) __nanosleep(200);
+        if (++idle > 4) __nanosleep(100);
         int late = 0;
         if (lane == 0 && (idle & 63) == 0) late = globaltimer_ns() - t_start > p.timeout_ns;
         if (__shfl_sync(0xffffffffu, late, 0)) {
@@ -345,7 +354,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_sweep_kernel(SweepPar
             break;
         }
     }
-    if (lane == 0 && p.visits && nvisits) atomicAdd(p.visits, nvisits);
+    if (lane == 0 && p.visits && nvisits) {
+        atomicAdd(p.visits, nvisits);
+        atomicAdd(p.visits + 1, niters);
+    }
 }
 
 cudaError_t launch_recon_sweep(const SweepParams &p, int conn, int num_sms, cudaStream_t s, int *grid_used)

@@ -42,7 +42,7 @@ struct SweepParams {
     uint32_t *flags;          // per tile: nonzero = must be visited
     uint32_t *pending;        // flagged + in-progress visits
     int32_t *err;             // device status word
-    uint32_t *visits;         // number of tile visits (statistics)
+    uint32_t *visits;         // [0] tile visits, [1] local iterations (statistics)
     int max_local;            // local iterations per visit before revisiting
     uint64_t timeout_ns;      // bound on the whole propagation
 };
