@@ -64,10 +64,10 @@ typedef enum {
 
 /* Propagation variants of rt_reconstruct; all give identical output. */
 enum {
-    RT_AUTO = 0,    /* library choice */
-    RT_RASTER = 1,  /* tile-resident directional sweeps over flagged tiles */
-    RT_QUEUE = 2,   /* pixel frontier queue (irregular wavefront propagation) */
-    RT_HYBRID = 3   /* sweeps while the frontier is large, then the queue */
+    RT_AUTO = 0,    /* library choice (RT_RASTER) */
+    RT_RASTER = 1,  /* directional sweeps of 32 x 64 tiles, revisiting flagged tiles */
+    RT_QUEUE = 2,   /* per-tile pixel FIFOs (irregular wavefront propagation) */
+    RT_HYBRID = 3   /* one sweep visit of every tile, then pixel FIFOs for what remains */
 };
 
 typedef struct rt_ctx rt_ctx;
@@ -179,14 +179,14 @@ enum {
  * ms[phase] and its number of bracketed intervals to count[phase] (arrays of
  * RT_NPHASES, either may be NULL), and forgets the records if reset != 0.
  * rt_kernel_launches returns how many kernels the context has launched.
- * rt_recon_stats waits for the device and reports how many tile visits and
- * local sweep iterations the last reconstruction made (statistics; 0 if
- * none); either pointer may be NULL.
+ * rt_recon_stats waits for the device and reports how many tile visits,
+ * dense sweep iterations and queue pops the last reconstruction made
+ * (statistics; 0 if none); any pointer may be NULL.
  */
 RT_API rt_status rt_timing_enable(rt_ctx *ctx, int enable);
 RT_API rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset);
 RT_API int64_t rt_kernel_launches(const rt_ctx *ctx);
-RT_API rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iterations);
+RT_API rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iterations, int64_t *pops);
 
 /* One tile of a batch. Every pointer is a device pointer. */
 typedef struct {
@@ -214,7 +214,7 @@ typedef struct {
     int conn_recon;  /* connectivity of the reconstruction (8) */
     int conn_fill;   /* connectivity of the background flood in fill-holes (4) */
     int variant;     /* reconstruction variant for every tile (RT_AUTO) */
-    int max_local;   /* local sweep iterations per tile visit; 0 = default (8) */
+    int max_local;   /* sweep iterations per dense tile visit; 0 = default */
 } rt_seg_params;
 
 /* Fill `p` with the defaults listed above. */

@@ -97,10 +97,11 @@ class Context:
         return lib().rt_kernel_launches(self._h)
 
     def recon_stats(self) -> tuple:
-        """(tile visits, local sweep iterations) of the last reconstruction."""
-        v, it = ctypes.c_int64(0), ctypes.c_int64(0)
-        _check(lib().rt_recon_stats(self._h, ctypes.byref(v), ctypes.byref(it)), "rt_recon_stats")
-        return v.value, it.value
+        """(tile visits, dense sweep iterations, queue pops) of the last reconstruction."""
+        v, it, pops = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().rt_recon_stats(self._h, ctypes.byref(v), ctypes.byref(it), ctypes.byref(pops)),
+               "rt_recon_stats")
+        return v.value, it.value, pops.value
 
     def close(self):
         if self._h:

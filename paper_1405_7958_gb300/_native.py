@@ -78,6 +78,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_timing_read.restype = _int
     lib.rt_kernel_launches.argtypes = [_vp]
     lib.rt_kernel_launches.restype = _i64
-    lib.rt_recon_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+    lib.rt_recon_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
     lib.rt_recon_stats.restype = _int
     return lib

@@ -140,7 +140,7 @@ rt_status cuda_status(cudaError_t e)
 // ---------------------------------------------------------------- recon
 struct ReconWs {
     uint32_t *flags;   // per tile
-    uint32_t *ctl;     // [0] pending, [1] visits, [2] local iterations
+    uint32_t *ctl;     // [0] pending, [1] visits, [2] dense iterations, [3] queue pops
     int32_t *err;
 };
 
@@ -157,16 +157,20 @@ void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w)
     }
 }
 
-// Enqueue init + sweeps for a batch whose buffers are carved. `err` receives
-// the device status.
-rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int max_local, int32_t *err,
+// Enqueue init + propagation for a batch whose buffers are carved. `err`
+// receives the device status.
+rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int variant, int max_local, int32_t *err,
                     cudaStream_t s)
 {
-    // every tile starts flagged (set by the init kernel with `pending`)
+    if (variant == RT_AUTO) variant = RT_RASTER;
+    // RT_RASTER / RT_QUEUE: every tile starts flagged for a dense visit (the
+    // queue visit then seeds every pixel); RT_HYBRID: nothing flagged, the
+    // dense pass over all tiles flags what remains.
+    const uint32_t flag0 = variant == RT_HYBRID ? 0u : 2u;
     RT_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, 8 * sizeof(uint32_t), s));
     {
         Phase ph(ctx, RT_PHASE_RECON_INIT, s);
-        RT_CUDA_TRY(launch_recon_init(b, w.flags, w.ctl, err, s));
+        RT_CUDA_TRY(launch_recon_init(b, w.flags, w.ctl, flag0, err, s));
         ctx->launches += 1;
     }
     ctx->visits_dev = w.ctl + 1;
@@ -177,12 +181,16 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int max_lo
     p.pending = w.ctl;
     p.err = err;
     p.visits = w.ctl + 1;
-    p.max_local = max_local > 0 ? max_local : 8;
+    p.max_local = max_local > 0 ? max_local : (variant == RT_HYBRID ? 64 : 8);
     p.timeout_ns = kSweepTimeoutNs;
     int grid = 0;
     Phase ph(ctx, RT_PHASE_RECON_SWEEP, s);
+    if (variant == RT_HYBRID) {
+        RT_CUDA_TRY(launch_recon_dense(p, conn, s));
+        ctx->launches += 1;
+    }
     ctx->launches += 1;
-    return cuda_status(launch_recon_sweep(p, conn, ctx->num_sms, s, &grid));
+    return cuda_status(launch_recon_persistent(p, conn, variant == RT_RASTER ? 0 : 1, ctx->num_sms, s, &grid));
 }
 
 void add_image(ReconBatch &b, const uint8_t *marker, int64_t ld_marker, const uint8_t *mask, int64_t ld_mask,
@@ -307,10 +315,10 @@ rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset)
 
 int64_t rt_kernel_launches(const rt_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
-rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iterations)
+rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iterations, int64_t *pops)
 {
     if (!ctx) return RT_EINVAL;
-    uint32_t v[2] = {0, 0};
+    uint32_t v[3] = {0, 0, 0};
     if (ctx->visits_dev) {
         DeviceGuard g(ctx->device);
         if (cudaMemcpy(v, ctx->visits_dev, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -320,6 +328,7 @@ rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iterations)
     }
     if (visits) *visits = v[0];
     if (iterations) *iterations = v[1];
+    if (pops) *pops = v[2];
     return RT_OK;
 }
 
@@ -349,7 +358,6 @@ rt_status rt_reconstruct(rt_ctx *ctx, const uint8_t *marker, int64_t ld_marker, 
     if (marker && marker != out && overlaps(out, span(H, ld_out, 1, W), marker, span(H, ld_marker, 1, W)))
         return RT_EINVAL;
     if (marker && marker == out && ld_marker != ld_out) return RT_EINVAL;
-    if (variant == RT_QUEUE || variant == RT_HYBRID) return RT_EUNAVAIL;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
 
@@ -367,7 +375,7 @@ rt_status rt_reconstruct(rt_ctx *ctx, const uint8_t *marker, int64_t ld_marker, 
 
     int32_t *err = dev_status ? dev_status : w.err;
     RT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
-    st = run_recon(ctx, b, w, conn, 0, err, s);
+    st = run_recon(ctx, b, w, conn, variant, 0, err, s);
     if (st != RT_OK) return st;
     Phase ph(ctx, RT_PHASE_RECON_OUT, s);
     ctx->launches += 1;
@@ -489,7 +497,6 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
     if (P.conn_fill != 4 && P.conn_fill != 8) return RT_EINVAL;
     if (P.h_offset < 0 || P.h_offset > 255 || P.threshold < 0 || P.threshold > 256) return RT_EINVAL;
     if (P.variant < RT_AUTO || P.variant > RT_HYBRID) return RT_EINVAL;
-    if (P.variant == RT_QUEUE || P.variant == RT_HYBRID) return RT_EUNAVAIL;
     int64_t maxN = 0;
     for (int i = 0; i < n; ++i) {
         const rt_tile &t = tiles[i];
@@ -542,7 +549,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         layout(cv, w, Bs, Fw, U, A, edt_ws);
 
         RT_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
-        st = run_recon(ctx, b, w, P.conn_recon, P.max_local, w.err, s);
+        st = run_recon(ctx, b, w, P.conn_recon, P.variant, P.max_local, w.err, s);
         if (st != RT_OK) return st;
         for (int i = 0; i < cn; ++i) {
             const rt_tile &t = tiles[c0 + i];

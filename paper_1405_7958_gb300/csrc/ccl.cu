@@ -231,12 +231,17 @@ __global__ void uf_flatten_kernel(UfArgs a, bool count_area, bool flag_border)
         const bool in = c < a.W;
         const int64_t p = (int64_t)r * a.W + c;
         int32_t root = -1;
-        if (in) {
-            const int32_t u = a.U[p];
-            if (u >= 0) {
-                root = find_g_halve(a.U, u);
-                if (root != u) atomicMin(a.U + p, root);
-            }
+        const int32_t u = in ? a.U[p] : -1;
+        // lanes holding the same value share one find
+        const unsigned has = __ballot_sync(0xffffffffu, u >= 0);
+        if (u >= 0) {
+            const unsigned same = __match_any_sync(has, u);
+            const int leader = __ffs(same) - 1;
+            if ((int)(threadIdx.x & 31) == leader) root = find_g_halve(a.U, u);
+            root = __shfl_sync(same, root, leader);
+            // plain store: the root is the smallest value any concurrent
+            // halving (atomicMin) could write here
+            if (root != u) a.U[p] = root;
         }
         if (count_area) {
             const unsigned act = __ballot_sync(0xffffffffu, root >= 0);

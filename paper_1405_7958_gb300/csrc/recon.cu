@@ -6,18 +6,24 @@
 // neighbour q, so the running image never exceeds the reconstruction and
 // only grows; any schedule of such updates that stops at a fixed point of
 // the 8- (or 4-) neighbourhood ends exactly at the reconstruction. The paper
-// runs the operation as an irregular wavefront propagation over active
-// elements; here the active elements are 32 x 64 tiles:
-//   * a warp visits a tile by loading it into registers as packed 16-bit
-//     pairs (lane = two columns, one register per row for R and for I),
-//     with a one-pixel halo from the current image;
-//   * it sweeps the tile until nothing changes: a down and an up sweep (each
-//     row takes the maximum of itself and the neighbouring pixels of the row
-//     just done), then a left-to-right and a right-to-left sweep along every
-//     row (rows transposed through shared memory so each lane walks one row);
-//   * it writes the tile back and flags the neighbouring tiles whose halo
-//     changed. A persistent kernel keeps visiting flagged tiles until no tile
-//     is flagged or being visited; there is no grid-wide barrier.
+// runs the operation as an irregular wavefront propagation (IWPP) over
+// active elements held in a hierarchical queue. Here the image is cut into
+// 32 x 64 tiles and the active elements are tiles (global level) and pixels
+// inside a tile (shared-memory level). Three schedules, same bytes:
+//   * dense visit: a warp loads the tile into registers as packed 16-bit
+//     pairs (lane = two columns, one register per row) and sweeps it (down,
+//     up, then along every row through shared memory) to its local fixed
+//     point;
+//   * queue visit: the warp loads the tile with its one-pixel halo into
+//     shared memory, seeds a FIFO with the pixels the halo can raise (or
+//     with every pixel), and propagates pixel by pixel with atomicMax,
+//     queueing each pixel that increases;
+//   * after a visit the warp writes the tile back and flags the neighbouring
+//     tiles whose halo changed. Persistent kernels keep visiting flagged
+//     tiles until no tile is flagged or being visited (no grid barrier).
+// RT_RASTER = dense visits only; RT_QUEUE = queue visits only, every tile
+// seeded with all its pixels; RT_HYBRID = one dense visit of every tile,
+// then queue visits for the tiles whose halo changed.
 #include "recon.cuh"
 
 namespace rtk {
@@ -26,15 +32,15 @@ constexpr int kWarpsPerCta = 4;
 constexpr int kTS = 33;                                  // transposed row stride (words)
 constexpr int kWarpWords = 2 * kTH * kTS + 2 * (kTH + 2);
 
-size_t sweep_smem_bytes() { return sizeof(uint32_t) * kWarpWords * kWarpsPerCta; }
 
 // ---------------------------------------------------------------- init
 // Iw = mask (0 in the padding), Rw = min(J, I). One thread per 4 pixels.
-__global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t *pending, int32_t *err)
+__global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t *pending, uint32_t flag0,
+                                  int32_t *err)
 {
     if (blockIdx.y == 0) {
-        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.ntiles; t += gridDim.x * blockDim.x) flags[t] = 1u;
-        if (blockIdx.x == 0 && threadIdx.x == 0) *pending = (uint32_t)b.ntiles;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.ntiles; t += gridDim.x * blockDim.x) flags[t] = flag0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) *pending = flag0 ? (uint32_t)b.ntiles : 0u;
     }
     const ReconImage &d = b.img[blockIdx.y];
     const int64_t wpr = d.Wp / 4;
@@ -70,14 +76,14 @@ __global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t 
     if (bad) raise_status(err, RT_EMARKER);
 }
 
-cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *pending, int32_t *err,
-                              cudaStream_t s)
+cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *pending, uint32_t flag0,
+                              int32_t *err, cudaStream_t s)
 {
     const int threads = 256;
     int64_t blocks = ceil_div(b.max_words, threads);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    recon_init_kernel<<<dim3((unsigned)blocks, (unsigned)b.n), threads, 0, s>>>(b, flags, pending, err);
+    recon_init_kernel<<<dim3((unsigned)blocks, (unsigned)b.n), threads, 0, s>>>(b, flags, pending, flag0, err);
     return cudaGetLastError();
 }
 
@@ -128,9 +134,40 @@ __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b)
 __device__ __forceinline__ uint32_t widen2(uint32_t v) { return __byte_perm(v, 0u, 0x4140); }
 __device__ __forceinline__ uint32_t narrow2(uint32_t w) { return __byte_perm(w, 0u, 0x4420); }
 
-__device__ __forceinline__ void mark_tile(uint32_t *flags, uint32_t *pending, int t)
+// Flag bits of a tile: its halo changed, or it needs a dense visit.
+constexpr uint32_t kHalo = 1u, kDense = 2u;
+
+__device__ __forceinline__ void mark_tile(uint32_t *flags, uint32_t *pending, int t, uint32_t bits = kHalo)
 {
-    if (atomicExch(flags + t, 1u) == 0u) atomicAdd(pending, 1u);
+    if (atomicOr(flags + t, bits) == 0u) atomicAdd(pending, 1u);
+}
+
+// Flags the neighbouring tiles that see a changed halo (and the tile itself
+// with `self_bits` when nonzero). Lane 0 only.
+template <int CONN>
+__device__ __forceinline__ void mark_neighbours(const SweepParams &p, const ReconImage &d, int t, int ty, int tx,
+                                                bool top, bool bot, bool left, bool right, bool tl, bool tr,
+                                                bool bl, bool br, uint32_t self_bits)
+{
+    const int nx = d.tiles_x, ny = d.tiles_y;
+    if (self_bits) mark_tile(p.flags, p.pending, t, self_bits);
+    if (top && ty > 0) mark_tile(p.flags, p.pending, t - 1);
+    if (bot && ty + 1 < ny) mark_tile(p.flags, p.pending, t + 1);
+    if (left && tx > 0) mark_tile(p.flags, p.pending, t - ny);
+    if (right && tx + 1 < nx) mark_tile(p.flags, p.pending, t + ny);
+    if (CONN == 8) {
+        if (tl && ty > 0 && tx > 0) mark_tile(p.flags, p.pending, t - ny - 1);
+        if (tr && ty > 0 && tx + 1 < nx) mark_tile(p.flags, p.pending, t + ny - 1);
+        if (bl && ty + 1 < ny && tx > 0) mark_tile(p.flags, p.pending, t - ny + 1);
+        if (br && ty + 1 < ny && tx + 1 < nx) mark_tile(p.flags, p.pending, t + ny + 1);
+    }
+}
+
+__device__ __forceinline__ const ReconImage &find_image(const SweepParams &p, int t)
+{
+    int k = 0;
+    while (k + 1 < p.b.n && t >= p.b.img[k + 1].tile_base) ++k;
+    return p.b.img[k];
 }
 
 struct WarpBuf {
@@ -142,23 +179,21 @@ struct WarpBuf {
 template <int CONN>
 __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, const WarpBuf &wb, int lane)
 {
-    int k = 0;
-    while (k + 1 < p.b.n && t >= p.b.img[k + 1].tile_base) ++k;
-    const ReconImage &d = p.b.img[k];
-    const int lt = t - d.tile_base;
-    const int ty = lt / d.tiles_x, tx = lt % d.tiles_x;
+    const ReconImage &d = find_image(p, t);
+    const int lt = t - d.tile_base;          // column-major: lt = tx * tiles_y + ty
+    const int ty = lt % d.tiles_y, tx = lt / d.tiles_y;
     const int r0 = ty * kTH, c0 = tx * kTW;
     const int64_t Wp = d.Wp;
     const uint16_t *Rg = reinterpret_cast<const uint16_t *>(d.Rw + (int64_t)r0 * Wp + c0) + lane;
     const uint16_t *Ig = reinterpret_cast<const uint16_t *>(d.Iw + (int64_t)r0 * Wp + c0) + lane;
     const int64_t ws = Wp / 2;   // row stride in 16-bit units
 
-    uint32_t R[kTH], I[kTH];
+    uint32_t R[kTH];
+    const uint32_t *Is = wb.sIT + lane;   // mask, row r at Is[r * kTS]
 #pragma unroll
     for (int r = 0; r < kTH; ++r) {
         R[r] = widen2(__ldcg(Rg + r * ws));
-        I[r] = widen2(__ldg(Ig + r * ws));
-        wb.sIT[r * kTS + lane] = I[r];
+        wb.sIT[r * kTS + lane] = widen2(__ldg(Ig + r * ws));
     }
     const uint32_t topw = r0 > 0 ? widen2(__ldcg(Rg - ws)) : 0u;
     const uint32_t botw = r0 + kTH < d.Hp ? widen2(__ldcg(Rg + kTH * ws)) : 0u;
@@ -174,9 +209,13 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
     }
     __syncwarp();
 
+    // Passes run in the cycle down, up, rows. Each pass is idempotent, so the
+    // tile is at a fixed point as soon as the two passes after the last one
+    // that changed something changed nothing.
     bool converged = false;
     int it = 0;
-    for (; it < p.max_local; ++it) {
+    int clean = 0;          // consecutive passes without a change
+    for (; it < p.max_local && !converged; ++it) {
         bool ch = false;
         // down sweep
         uint32_t prev = topw;
@@ -190,11 +229,17 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
                 if (lane == 31) sr = wb.sHR[r];
                 m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
             }
-            const uint32_t nv = vmin2(m, I[r]);
+            const uint32_t nv = vmin2(m, Is[r * kTS]);
             ch |= nv != R[r];
             R[r] = nv;
             prev = nv;
         }
+        clean = __any_sync(0xffffffffu, ch) ? 0 : clean + 1;
+        if (clean >= 2) {
+            converged = true;
+            break;
+        }
+        ch = false;
         // up sweep
         prev = botw;
 #pragma unroll
@@ -207,11 +252,17 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
                 if (lane == 31) sr = wb.sHR[r + 2];
                 m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
             }
-            const uint32_t nv = vmin2(m, I[r]);
+            const uint32_t nv = vmin2(m, Is[r * kTS]);
             ch |= nv != R[r];
             R[r] = nv;
             prev = nv;
         }
+        clean = __any_sync(0xffffffffu, ch) ? 0 : clean + 1;
+        if (clean >= 2 && it > 0) {
+            converged = true;
+            break;
+        }
+        ch = false;
         // left-to-right and right-to-left along every row (lane = row)
 #pragma unroll
         for (int r = 0; r < kTH; ++r) wb.sRT[r * kTS + lane] = R[r];
@@ -248,11 +299,8 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
 #pragma unroll
         for (int r = 0; r < kTH; ++r) R[r] = wb.sRT[r * kTS + lane];
         __syncwarp();
-        if (!__any_sync(0xffffffffu, ch)) {
-            converged = true;
-            ++it;
-            break;
-        }
+        clean = __any_sync(0xffffffffu, ch) ? 0 : clean + 1;
+        if (clean >= 2) converged = true;
     }
 
     // write back, and find which borders moved
@@ -279,60 +327,237 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
     const bool bl = __shfl_sync(0xffffffffu, dbot & 0xffffu, 0) != 0;
     const bool br = __shfl_sync(0xffffffffu, dbot >> 16, 31) != 0;
     __threadfence();
-    if (lane == 0) {
-        const int nx = d.tiles_x, ny = d.tiles_y, base = d.tile_base;
-        if (!converged) mark_tile(p.flags, p.pending, t);
-        if (top && ty > 0) mark_tile(p.flags, p.pending, base + lt - nx);
-        if (bot && ty + 1 < ny) mark_tile(p.flags, p.pending, base + lt + nx);
-        if (left && tx > 0) mark_tile(p.flags, p.pending, base + lt - 1);
-        if (right && tx + 1 < nx) mark_tile(p.flags, p.pending, base + lt + 1);
-        if (CONN == 8) {
-            if (tl && ty > 0 && tx > 0) mark_tile(p.flags, p.pending, base + lt - nx - 1);
-            if (tr && ty > 0 && tx + 1 < nx) mark_tile(p.flags, p.pending, base + lt - nx + 1);
-            if (bl && ty + 1 < ny && tx > 0) mark_tile(p.flags, p.pending, base + lt + nx - 1);
-            if (br && ty + 1 < ny && tx + 1 < nx) mark_tile(p.flags, p.pending, base + lt + nx + 1);
-        }
-    }
+    if (lane == 0)
+        mark_neighbours<CONN>(p, d, t, ty, tx, top, bot, left, right, tl, tr, bl, br, converged ? 0u : kDense);
     return (uint32_t)it;
 }
 
-// Persistent propagation. Warp w owns tiles w, w + nwarps, ...; it visits
-// those flagged, and leaves when nothing is flagged or being visited
-// anywhere. A visit is counted in `pending` from the moment its tile is
-// flagged until after the visit has flagged its neighbours, so pending = 0
-// means the image is at the fixed point. The launch is cooperative only to
-// guarantee that every warp is resident (a flagged tile's owner always runs).
+// ------------------------------------------------------------ queue visit
+constexpr int kQW = kTW + 2;           // padded row (halo columns included)
+constexpr int kQCap = kTH * kTW;       // one slot per pixel of the tile
+constexpr int kQWords = (kTH + 2) * kQW + kTH * kTW / 4 + kQCap / 2 + kQCap / 32 + 1;
+constexpr uint32_t kMaxPops = 64u * kQCap;   // bound on one queue visit
+
+struct QBuf {
+    uint32_t *R;     // (kTH + 2) x kQW, one pixel per word, halo included
+    uint8_t *I;      // kTH x kTW mask
+    uint16_t *q;     // FIFO of pixel indices r * kTW + c
+    uint32_t *inq;   // one bit per pixel: queued
+    uint32_t *tail;  // FIFO tail
+};
+
+__device__ __forceinline__ void q_push(const QBuf &qb, int idx)
+{
+    const uint32_t bit = 1u << (idx & 31);
+    if (!(atomicOr(qb.inq + (idx >> 5), bit) & bit)) {
+        const uint32_t pos = atomicAdd(qb.tail, 1u);
+        qb.q[pos & (kQCap - 1)] = (uint16_t)idx;
+    }
+}
+
+// Raise pixel (r, c) of the tile to min(v, I) if that is larger; queue it if
+// it grew.
+__device__ __forceinline__ void q_relax(const QBuf &qb, int r, int c, uint32_t v)
+{
+    const uint32_t cand = min(v, (uint32_t)qb.I[r * kTW + c]);
+    uint32_t *a = qb.R + (r + 1) * kQW + c + 1;
+    if (cand > *reinterpret_cast<volatile uint32_t *>(a)) {
+        if (atomicMax(a, cand) < cand) q_push(qb, r * kTW + c);
+    }
+}
+
 template <int CONN>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) recon_sweep_kernel(SweepParams p)
+__device__ __forceinline__ uint32_t visit_queue(const SweepParams &p, int t, uint32_t bits, const QBuf &qb, int lane)
+{
+    const ReconImage &d = find_image(p, t);
+    const int lt = t - d.tile_base;
+    const int ty = lt % d.tiles_y, tx = lt / d.tiles_y;
+    const int r0 = ty * kTH, c0 = tx * kTW;
+    const int64_t Wp = d.Wp;
+    volatile uint32_t *vR = qb.R;
+
+    // stage R with its halo (rows r0-1 .. r0+kTH) and the mask
+    for (int i = 0; i < kTH + 2; ++i) {
+        const int r = r0 - 1 + i;
+        uint32_t w = 0;
+        if (r >= 0 && r < d.Hp) w = __ldcg(reinterpret_cast<const uint16_t *>(d.Rw + (int64_t)r * Wp + c0) + lane);
+        qb.R[i * kQW + 1 + 2 * lane] = w & 0xffu;
+        qb.R[i * kQW + 2 + 2 * lane] = w >> 8;
+    }
+    for (int i = lane; i < kTH + 2; i += 32) {
+        const int r = r0 - 1 + i;
+        uint32_t hl = 0, hr = 0;
+        if (r >= 0 && r < d.Hp) {
+            if (c0 > 0) hl = __ldcg(d.Rw + (int64_t)r * Wp + c0 - 1);
+            if (c0 + kTW < Wp) hr = __ldcg(d.Rw + (int64_t)r * Wp + c0 + kTW);
+        }
+        qb.R[i * kQW] = hl;
+        qb.R[i * kQW + kQW - 1] = hr;
+    }
+    for (int r = 0; r < kTH; ++r)
+        reinterpret_cast<uint16_t *>(qb.I + r * kTW)[lane] =
+            __ldg(reinterpret_cast<const uint16_t *>(d.Iw + (int64_t)(r0 + r) * Wp + c0) + lane);
+    for (int i = lane; i < kQCap / 32; i += 32) qb.inq[i] = 0u;
+    if (lane == 0) *qb.tail = 0u;
+    __syncwarp();
+
+    if (bits & kDense) {
+        // every pixel is active
+        for (int i = lane; i < kQCap / 32; i += 32) qb.inq[i] = 0xffffffffu;
+        for (int i = lane; i < kQCap; i += 32) qb.q[i] = (uint16_t)i;
+        if (lane == 0) *qb.tail = kQCap;
+        __syncwarp();
+    }
+    // the border pixels the halo can raise: top and bottom rows, then the
+    // left and right columns (values flow into the tile only here)
+    for (int pos = lane; pos < 2 * kTW + 2 * kTH; pos += 32) {
+        int r, c;
+        if (pos < kTW) { r = 0; c = pos; }
+        else if (pos < 2 * kTW) { r = kTH - 1; c = pos - kTW; }
+        else if (pos < 2 * kTW + kTH) { r = pos - 2 * kTW; c = 0; }
+        else { r = pos - 2 * kTW - kTH; c = kTW - 1; }
+        const int a = (r + 1) * kQW + c + 1;
+        uint32_t m = max(max(vR[a - kQW], vR[a + kQW]), max(vR[a - 1], vR[a + 1]));
+        if (CONN == 8) m = max(m, max(max(vR[a - kQW - 1], vR[a - kQW + 1]), max(vR[a + kQW - 1], vR[a + kQW + 1])));
+        const uint32_t cand = min(m, (uint32_t)qb.I[r * kTW + c]);
+        if (cand > vR[a] && atomicMax(qb.R + a, cand) < cand) q_push(qb, r * kTW + c);
+    }
+    __syncwarp();
+
+    // FIFO propagation, up to 32 pixels per step
+    uint32_t head = 0, pops = 0;
+    uint32_t tail = *reinterpret_cast<volatile uint32_t *>(qb.tail);
+    while (head < tail && pops < kMaxPops) {
+        const uint32_t n = min(32u, tail - head);
+        int idx = -1;
+        if ((uint32_t)lane < n) idx = qb.q[(head + lane) & (kQCap - 1)];
+        __syncwarp();   // every slot of this step is read before any push of it
+        if (idx >= 0) {
+            atomicAnd(qb.inq + (idx >> 5), ~(1u << (idx & 31)));
+            __threadfence_block();
+            const int r = idx / kTW, c = idx % kTW;
+            const uint32_t v = vR[(r + 1) * kQW + c + 1];
+            if (r > 0) q_relax(qb, r - 1, c, v);
+            if (r + 1 < kTH) q_relax(qb, r + 1, c, v);
+            if (c > 0) q_relax(qb, r, c - 1, v);
+            if (c + 1 < kTW) q_relax(qb, r, c + 1, v);
+            if (CONN == 8) {
+                if (r > 0 && c > 0) q_relax(qb, r - 1, c - 1, v);
+                if (r > 0 && c + 1 < kTW) q_relax(qb, r - 1, c + 1, v);
+                if (r + 1 < kTH && c > 0) q_relax(qb, r + 1, c - 1, v);
+                if (r + 1 < kTH && c + 1 < kTW) q_relax(qb, r + 1, c + 1, v);
+            }
+        }
+        head += n;
+        pops += n;
+        __syncwarp();
+        tail = *reinterpret_cast<volatile uint32_t *>(qb.tail);
+    }
+    if (head < tail && lane == 0) raise_status(p.err, RT_ETIMEOUT);
+
+    // write back, and find which borders moved
+    uint16_t *Rs = reinterpret_cast<uint16_t *>(d.Rw + (int64_t)r0 * Wp + c0) + lane;
+    const int64_t ws = Wp / 2;
+    uint32_t dl = 0, dr = 0, dtop = 0, dbot = 0, any = 0;
+    for (int r = 0; r < kTH; ++r) {
+        const uint32_t orig = __ldcg(Rs + r * ws);
+        const uint32_t nv = vR[(r + 1) * kQW + 1 + 2 * lane] | (vR[(r + 1) * kQW + 2 + 2 * lane] << 8);
+        const uint32_t diff = orig ^ nv;
+        if (diff) __stcg(Rs + r * ws, (uint16_t)nv);
+        dl |= diff & 0xffu;
+        dr |= diff >> 8;
+        any |= diff;
+        if (r == 0) dtop = diff;
+        if (r == kTH - 1) dbot = diff;
+    }
+    if (!__any_sync(0xffffffffu, any != 0)) return pops;
+    const bool top = __any_sync(0xffffffffu, dtop != 0);
+    const bool bot = __any_sync(0xffffffffu, dbot != 0);
+    const bool left = __shfl_sync(0xffffffffu, dl, 0) != 0;
+    const bool right = __shfl_sync(0xffffffffu, dr, 31) != 0;
+    const bool tl = __shfl_sync(0xffffffffu, dtop & 0xffu, 0) != 0;
+    const bool tr = __shfl_sync(0xffffffffu, dtop >> 8, 31) != 0;
+    const bool bl = __shfl_sync(0xffffffffu, dbot & 0xffu, 0) != 0;
+    const bool br = __shfl_sync(0xffffffffu, dbot >> 8, 31) != 0;
+    __threadfence();
+    if (lane == 0) mark_neighbours<CONN>(p, d, t, ty, tx, top, bot, left, right, tl, tr, bl, br, 0u);
+    return pops;
+}
+
+// ------------------------------------------------------------- kernels
+// One dense visit of every tile (first phase of RT_HYBRID).
+template <int CONN>
+__global__ void __launch_bounds__(kWarpsPerCta * 32) recon_dense_kernel(SweepParams p)
 {
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * kWarpsPerCta + warp;
+    if (t >= p.ntiles) return;
     WarpBuf wb;
     wb.sRT = smem + warp * kWarpWords;
     wb.sIT = wb.sRT + kTH * kTS;
     wb.sHL = wb.sIT + kTH * kTS;
     wb.sHR = wb.sHL + (kTH + 2);
+    const uint32_t it = visit_tile<CONN>(p, t, wb, lane);
+    if (lane == 0 && p.visits) {
+        atomicAdd(p.visits, 1u);
+        atomicAdd(p.visits + 1, it);
+    }
+}
+
+// Persistent propagation. Warp w owns a contiguous run of tiles (tiles are
+// numbered column by column, so a run is a vertical strip); it visits those
+// flagged, and leaves when nothing is flagged or being visited anywhere. A
+// visit is counted in `pending` from the moment its tile is flagged until
+// after the visit has flagged its neighbours, so pending = 0 means the image
+// is at the fixed point. The launch is cooperative only to guarantee that
+// every warp is resident (a flagged tile's owner always runs).
+// QUEUE = 0: dense visits; QUEUE = 1: queue visits.
+template <int CONN, int QUEUE>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 5) recon_persistent_kernel(SweepParams p)
+{
+    extern __shared__ uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpBuf wb;
+    QBuf qb;
+    if (QUEUE) {
+        uint32_t *base = smem + warp * kQWords;
+        qb.R = base;
+        qb.I = reinterpret_cast<uint8_t *>(base + (kTH + 2) * kQW);
+        qb.q = reinterpret_cast<uint16_t *>(base + (kTH + 2) * kQW + kTH * kTW / 4);
+        qb.inq = base + (kTH + 2) * kQW + kTH * kTW / 4 + kQCap / 2;
+        qb.tail = qb.inq + kQCap / 32;
+    } else {
+        wb.sRT = smem + warp * kWarpWords;
+        wb.sIT = wb.sRT + kTH * kTS;
+        wb.sHL = wb.sIT + kTH * kTS;
+        wb.sHR = wb.sHL + (kTH + 2);
+    }
     const int gw = blockIdx.x * kWarpsPerCta + warp;
     const int nw = gridDim.x * kWarpsPerCta;
+    const int chunk = (p.ntiles + nw - 1) / nw;
+    const int own0 = gw * chunk;
+    const int own1 = min(p.ntiles, own0 + chunk);
     const uint64_t t_start = globaltimer_ns();
-    uint32_t nvisits = 0, niters = 0;
+    uint32_t nvisits = 0, work = 0;
     int idle = 0;
     for (;;) {
         bool did = false;
-        // the warp's tiles, 32 flags per load
-        for (int base = gw; base < p.ntiles; base += nw * 32) {
-            const int tl = base + lane * nw;
-            const bool f = tl < p.ntiles && *reinterpret_cast<volatile uint32_t *>(p.flags + tl) != 0u;
+        for (int base = own0; base < own1; base += 32) {
+            const int tl = base + lane;
+            const bool f = tl < own1 && *reinterpret_cast<volatile uint32_t *>(p.flags + tl) != 0u;
             uint32_t mask = __ballot_sync(0xffffffffu, f);
             while (mask) {
                 const int i = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const int t = base + i * nw;
+                const int t = base + i;
                 uint32_t got = 0;
                 if (lane == 0) got = atomicExch(p.flags + t, 0u);
-                if (!__shfl_sync(0xffffffffu, got, 0)) continue;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) continue;
                 __threadfence();
-                niters += visit_tile<CONN>(p, t, wb, lane);
+                if (QUEUE) work += visit_queue<CONN>(p, t, got, qb, lane);
+                else work += visit_tile<CONN>(p, t, wb, lane);
                 if (lane == 0) atomicSub(p.pending, 1u);
                 did = true;
                 ++nvisits;
@@ -356,14 +581,31 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_sweep_kernel(SweepPar
     }
     if (lane == 0 && p.visits && nvisits) {
         atomicAdd(p.visits, nvisits);
-        atomicAdd(p.visits + 1, niters);
+        atomicAdd(p.visits + (QUEUE ? 2 : 1), work);
     }
 }
 
-cudaError_t launch_recon_sweep(const SweepParams &p, int conn, int num_sms, cudaStream_t s, int *grid_used)
+size_t recon_smem_bytes(int queue) { return sizeof(uint32_t) * (queue ? kQWords : kWarpWords) * kWarpsPerCta; }
+
+cudaError_t launch_recon_dense(const SweepParams &p, int conn, cudaStream_t s)
 {
-    const size_t smem = sweep_smem_bytes();
-    const void *fn = conn == 8 ? (const void *)recon_sweep_kernel<8> : (const void *)recon_sweep_kernel<4>;
+    const size_t smem = recon_smem_bytes(0);
+    const void *fn = conn == 8 ? (const void *)recon_dense_kernel<8> : (const void *)recon_dense_kernel<4>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    SweepParams pp = p;
+    void *args[] = {&pp};
+    return cudaLaunchKernel(fn, dim3((unsigned)ceil_div(p.ntiles, kWarpsPerCta)), dim3(kWarpsPerCta * 32), args,
+                            smem, s);
+}
+
+cudaError_t launch_recon_persistent(const SweepParams &p, int conn, int queue, int num_sms, cudaStream_t s,
+                                    int *grid_used)
+{
+    const size_t smem = recon_smem_bytes(queue);
+    const void *fn;
+    if (queue) fn = conn == 8 ? (const void *)recon_persistent_kernel<8, 1> : (const void *)recon_persistent_kernel<4, 1>;
+    else fn = conn == 8 ? (const void *)recon_persistent_kernel<8, 0> : (const void *)recon_persistent_kernel<4, 0>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

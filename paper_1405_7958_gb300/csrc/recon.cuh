@@ -42,19 +42,21 @@ struct SweepParams {
     uint32_t *flags;          // per tile: nonzero = must be visited
     uint32_t *pending;        // flagged + in-progress visits
     int32_t *err;             // device status word
-    uint32_t *visits;         // [0] tile visits, [1] local iterations (statistics)
+    uint32_t *visits;         // [0] tile visits, [1] dense iterations, [2] queue pops (statistics)
     int max_local;            // local iterations per visit before revisiting
     uint64_t timeout_ns;      // bound on the whole propagation
 };
 
-size_t sweep_smem_bytes();
 void plan_recon_image(ReconImage &d, int H, int W);
 cudaError_t launch_marker(const uint8_t *mask, int64_t ld_mask, uint8_t *marker, int64_t ld_marker, int H,
                           int W, int h_offset, cudaStream_t s);
-cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *pending, int32_t *err,
-                              cudaStream_t s);
-cudaError_t launch_recon_sweep(const SweepParams &p, int conn, int num_sms, cudaStream_t s,
-                               int *grid_used);
+cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *pending, uint32_t flag0,
+                              int32_t *err, cudaStream_t s);
+// one dense visit of every tile (non-persistent)
+cudaError_t launch_recon_dense(const SweepParams &p, int conn, cudaStream_t s);
+// persistent visits of flagged tiles until quiescence; queue = 1: queue visits
+cudaError_t launch_recon_persistent(const SweepParams &p, int conn, int queue, int num_sms, cudaStream_t s,
+                                    int *grid_used);
 cudaError_t launch_recon_out(const uint8_t *Rw, int Wp, uint8_t *out, int64_t ld_out, int H, int W,
                              uint8_t *bin, int64_t ld_bin, int threshold, cudaStream_t s);
 

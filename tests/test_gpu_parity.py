@@ -56,15 +56,20 @@ def test_recon_config1(rt):
     assert np.array_equal(host(rt.reconstruct(dev(I), J, conn=8)), want)
 
 
+VARIANTS = ["RT_RASTER", "RT_QUEUE", "RT_HYBRID"]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("conn", [4, 8])
-def test_recon_random_sizes(rt, conn):
+def test_recon_random_sizes(rt, conn, variant):
     rng = np.random.default_rng(7)
     for H, W in SIZES:
         I = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
         J = np.minimum(I, rng.integers(0, 256, size=(H, W))).astype(np.uint8)
         J[rng.random((H, W)) < 0.98] = 0
         want = oracle.recon(J, I, conn)
-        assert np.array_equal(host(rt.reconstruct(dev(I), dev(J), conn=conn)), want), (H, W)
+        got = host(rt.reconstruct(dev(I), dev(J), conn=conn, variant=getattr(rt, variant)))
+        assert np.array_equal(got, want), (H, W)
 
 
 def test_recon_strided_and_alias(rt):
@@ -89,20 +94,23 @@ def test_recon_marker_above_mask_reports_and_clamps(rt):
     assert int(st.item()) == rt.RT_EMARKER
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("conn", [4, 8])
-def test_recon_adversarial(rt, conn):
+def test_recon_adversarial(rt, conn, variant):
     cases = [synth.spiral(129, low=0), synth.serpentine(131, 200), synth.checkerboard(97, 161, 0, 200),
              np.zeros((70, 90), np.uint8), np.full((70, 90), 255, np.uint8)]
     for I in cases:
         J = np.zeros_like(I)
         J[0, 0] = I[0, 0]
-        assert np.array_equal(host(rt.reconstruct(dev(I), dev(J), conn=conn)), oracle.recon(J, I, conn))
+        got = host(rt.reconstruct(dev(I), dev(J), conn=conn, variant=getattr(rt, variant)))
+        assert np.array_equal(got, oracle.recon(J, I, conn))
 
 
-def test_recon_full_4k_tile(rt):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_recon_full_4k_tile(rt, variant):
     I = synth.config2_tile(2000)
     want = oracle.recon(oracle.marker(I, 30), I, 8)
-    got = host(rt.reconstruct(dev(I), None, h_offset=30, conn=8))
+    got = host(rt.reconstruct(dev(I), None, h_offset=30, conn=8, variant=getattr(rt, variant)))
     assert np.array_equal(got, want)
 
 
@@ -205,11 +213,12 @@ def test_chain_full_4k(rt):
     check_chain(out, I)
 
 
-def test_chain_independent_of_local_iterations(rt):
-    """Bytes do not depend on how the propagation is scheduled."""
+def test_chain_independent_of_schedule(rt):
+    """Bytes do not depend on the variant or on how the propagation is scheduled."""
     I = synth.config2_tile(31, H=700, W=900)
-    a = rt.segment_batch([dev(I)], rt.SegParams(max_local=1))[0]
-    b = rt.segment_batch([dev(I)], rt.SegParams(max_local=32))[0]
-    for k in ("R", "F", "L", "D"):
-        assert np.array_equal(host(a[k]), host(b[k]))
-    check_chain(a, I)
+    runs = [rt.segment_batch([dev(I)], rt.SegParams(variant=getattr(rt, v), max_local=m))[0]
+            for v in VARIANTS for m in (1, 32)]
+    for other in runs[1:]:
+        for k in ("R", "F", "L", "D"):
+            assert np.array_equal(host(runs[0][k]), host(other[k]))
+    check_chain(runs[0], I)
