@@ -59,7 +59,8 @@ typedef enum {
     RT_ETIMEOUT = 4,  /* device-side iteration or wait bound reached */
     RT_EMARKER = 5,   /* marker above the mask somewhere (output still defined) */
     RT_EQUEUE = 6,    /* frontier queue overflow that the fall-back could not absorb */
-    RT_EUNAVAIL = 7   /* requested variant or feature not available */
+    RT_EUNAVAIL = 7,  /* requested variant or feature not available */
+    RT_ESIZE = 8      /* image larger than the fixed scratch of rt_edt_noalloc */
 } rt_status;
 
 /* Propagation variants of rt_reconstruct; all give identical output. */
@@ -187,6 +188,27 @@ RT_API rt_status rt_timing_enable(rt_ctx *ctx, int enable);
 RT_API rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset);
 RT_API int64_t rt_kernel_launches(const rt_ctx *ctx);
 RT_API rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iterations, int64_t *pops);
+
+/*
+ * The same squared EDT as rt_edt, for callers that must not allocate device
+ * memory while they run: for instance a serving loop that reserved its whole
+ * memory budget at start-up, or a plug-in inside a host application that
+ * owns every device allocation. For them a cudaMalloc can fail at the worst
+ * moment and it synchronises the whole device. This entry point has no
+ * counterpart in the paper; it exists only for such callers.
+ *
+ * No context and no allocation: the scratch is a fixed array built into the
+ * library (about 2.5 MiB, held on every GPU that loads the library until
+ * the process exits), so images are limited to H * W <= 1,048,576 pixels
+ * (and W <= 32768); larger ones return RT_ESIZE. It runs on the current
+ * device; the first call on a device looks the array's address up once, so
+ * make that first call before any stream capture. All calls share the one
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. Arguments,
+ * output and status are as for rt_edt.
+ */
+RT_API rt_status rt_edt_noalloc(const uint8_t *fg, int64_t ld_fg, int32_t *d2, int64_t ld_d2,
+                                int H, int W, int32_t *dev_status, void *stream);
 
 /* One tile of a batch. Every pointer is a device pointer. */
 typedef struct {

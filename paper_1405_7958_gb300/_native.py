@@ -10,7 +10,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librtseg.so")
 
-RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT, RT_EMARKER, RT_EQUEUE, RT_EUNAVAIL = range(8)
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT, RT_EMARKER, RT_EQUEUE, RT_EUNAVAIL, RT_ESIZE = range(9)
 RT_AUTO, RT_RASTER, RT_QUEUE, RT_HYBRID = range(4)
 
 # every symbol declared in include/rt.h
@@ -18,6 +18,7 @@ EXPORTS = (
     "rt_create", "rt_destroy", "rt_status_str", "rt_version", "rt_workspace_bytes", "rt_marker",
     "rt_reconstruct", "rt_fill_holes", "rt_label_area", "rt_edt", "rt_seg_params_default",
     "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_recon_stats",
+    "rt_edt_noalloc",
 )
 RT_NPHASES = 6
 PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt")
@@ -68,6 +69,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_label_area.restype = _int
     lib.rt_edt.argtypes = [_vp, _vp, _i64, _vp, _i64, _int, _int, _vp, _vp]
     lib.rt_edt.restype = _int
+    lib.rt_edt_noalloc.argtypes = [_vp, _i64, _vp, _i64, _int, _int, _vp, _vp]
+    lib.rt_edt_noalloc.restype = _int
     lib.rt_seg_params_default.argtypes = [ctypes.POINTER(RtSegParams)]
     lib.rt_seg_params_default.restype = None
     lib.rt_segment_batch.argtypes = [_vp, ctypes.POINTER(RtTile), _int, ctypes.POINTER(RtSegParams), _vp]

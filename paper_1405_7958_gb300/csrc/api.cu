@@ -234,6 +234,7 @@ const char *rt_status_str(int status)
     case RT_EMARKER: return "RT_EMARKER: marker above mask (clamped)";
     case RT_EQUEUE: return "RT_EQUEUE: frontier queue overflow";
     case RT_EUNAVAIL: return "RT_EUNAVAIL: variant or feature unavailable";
+    case RT_ESIZE: return "RT_ESIZE: image larger than the fixed scratch of the allocation-free entry point";
     default: return "unknown rt_status";
     }
 }
