@@ -211,6 +211,18 @@ void add_image(ReconBatch &b, const uint8_t *marker, int64_t ld_marker, const ui
     b.n++;
 }
 
+// Union-find workspace for an H x W image.
+void carve_uf(Carve &cv, UfArgs &a, int H, int W)
+{
+    const size_t N = (size_t)H * W;
+    const size_t nblk = (size_t)ceil_div(W, kUfBlock) * ceil_div(H, kUfBlock);
+    a.U = cv.take<int32_t>(N);
+    a.A = cv.take<int32_t>(N);
+    a.edge = cv.take<int32_t>(nblk * kUfEdge);
+    a.list = cv.take<int32_t>(N / 2 + 2);
+    a.nlist = cv.take<uint32_t>(1);
+}
+
 __global__ void copy_status_kernel(const int32_t *src, int32_t *dst)
 {
     if (threadIdx.x == 0 && *src != 0) atomicCAS(dst, 0, *src);
@@ -393,26 +405,23 @@ rt_status rt_fill_holes(rt_ctx *ctx, const uint8_t *in, int64_t ld_in, uint8_t *
     if ((const void *)in == (const void *)out && ld_in != ld_out) return RT_EINVAL;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t N = (size_t)H * W;
+    UfArgs a;
     Carve cv;
-    cv.take<int32_t>(N);
-    cv.take<int32_t>(N);
+    carve_uf(cv, a, H, W);
     rt_status st = ensure_ws(ctx, cv.off);
     if (st != RT_OK) return st;
     cv = Carve();
     cv.base = (char *)ctx->ws;
-    UfArgs a;
+    carve_uf(cv, a, H, W);
     a.in = in;
     a.ld_in = ld_in;
     a.H = H;
     a.W = W;
-    a.U = cv.take<int32_t>(N);
-    a.A = cv.take<int32_t>(N);
     if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
     Phase ph(ctx, RT_PHASE_FILL, s);
     ctx->launches += 4;
     RT_CUDA_TRY(uf_build(a, conn, kFgZero, false, true, s));
-    return cuda_status(uf_fill_out(a, out, ld_out, s));
+    return cuda_status(uf_fill_out(a, conn, out, ld_out, s));
 }
 
 rt_status rt_label_area(rt_ctx *ctx, const uint8_t *bin, int64_t ld_bin, int32_t *labels, int64_t ld_lab, int H,
@@ -424,27 +433,24 @@ rt_status rt_label_area(rt_ctx *ctx, const uint8_t *bin, int64_t ld_bin, int32_t
     if (overlaps(bin, span(H, ld_bin, 1, W), labels, span(H, ld_lab, 4, W))) return RT_EINVAL;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t N = (size_t)H * W;
+    UfArgs a;
     Carve cv;
-    cv.take<int32_t>(N);
-    cv.take<int32_t>(N);
+    carve_uf(cv, a, H, W);
     rt_status st = ensure_ws(ctx, cv.off);
     if (st != RT_OK) return st;
     cv = Carve();
     cv.base = (char *)ctx->ws;
-    UfArgs a;
+    carve_uf(cv, a, H, W);
     a.in = bin;
     a.ld_in = ld_bin;
     a.H = H;
     a.W = W;
-    a.U = cv.take<int32_t>(N);
-    a.A = cv.take<int32_t>(N);
     if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
     if (dev_n_kept) RT_CUDA_TRY(cudaMemsetAsync(dev_n_kept, 0, sizeof(int32_t), s));
     Phase ph(ctx, RT_PHASE_LABEL, s);
     ctx->launches += 4;
     RT_CUDA_TRY(uf_build(a, conn, kFgNonzero, true, false, s));
-    return cuda_status(uf_labels_out(a, labels, ld_lab, min_area, max_area, dev_n_kept, s));
+    return cuda_status(uf_labels_out(a, conn, labels, ld_lab, min_area, max_area, dev_n_kept, s));
 }
 
 rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int64_t ld_d2, int H, int W,
@@ -521,33 +527,32 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         }
         // workspace: recon buffers for the chunk, binary B per tile, then one
         // shared set of union-find / EDT buffers (tiles run one after another)
-        auto layout = [&](Carve &cv, ReconWs &w, std::vector<uint8_t *> &Bs, uint8_t *&Fw, int32_t *&U,
-                          int32_t *&A, char *&edt_ws) {
+        int maxH = 0, maxW = 0;
+        for (int i = 0; i < cn; ++i) {
+            maxH = b.img[i].H > maxH ? b.img[i].H : maxH;
+            maxW = b.img[i].W > maxW ? b.img[i].W : maxW;
+        }
+        auto layout = [&](Carve &cv, ReconWs &w, std::vector<uint8_t *> &Bs, uint8_t *&Fw, char *&uf_ws,
+                          char *&edt_ws) {
             carve_recon(cv, b, w);
             Bs.resize(cn);
             for (int i = 0; i < cn; ++i) Bs[i] = cv.take<uint8_t>((size_t)b.img[i].H * b.img[i].W);
             Fw = cv.take<uint8_t>((size_t)maxN);
-            U = cv.take<int32_t>((size_t)maxN);
-            A = cv.take<int32_t>((size_t)maxN);
-            int maxH = 0, maxW = 0;
-            for (int i = 0; i < cn; ++i) {
-                maxH = b.img[i].H > maxH ? b.img[i].H : maxH;
-                maxW = b.img[i].W > maxW ? b.img[i].W : maxW;
-            }
+            // union-find pieces sized for (maxH, maxW), enough for every tile of the chunk
+            uf_ws = cv.take<char>(uf_workspace_bytes(maxH, maxW));
             edt_ws = cv.take<char>(edt_workspace_bytes(maxH, maxW) + (size_t)maxN * 2);
         };
         Carve cv;
         ReconWs w;
         std::vector<uint8_t *> Bs;
         uint8_t *Fw;
-        int32_t *U, *A;
-        char *edt_ws;
-        layout(cv, w, Bs, Fw, U, A, edt_ws);
+        char *uf_ws, *edt_ws;
+        layout(cv, w, Bs, Fw, uf_ws, edt_ws);
         rt_status st = ensure_ws(ctx, cv.off);
         if (st != RT_OK) return st;
         cv = Carve();
         cv.base = (char *)ctx->ws;
-        layout(cv, w, Bs, Fw, U, A, edt_ws);
+        layout(cv, w, Bs, Fw, uf_ws, edt_ws);
 
         RT_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
         st = run_recon(ctx, b, w, P.conn_recon, P.variant, P.max_local, w.err, s);
@@ -562,19 +567,20 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
                 RT_CUDA_TRY(launch_recon_out(d.Rw, d.Wp, t.recon, t.ld_recon, H, W, Bs[i], W, P.threshold, s));
             }
             UfArgs fa;
+            Carve uc;
+            uc.base = uf_ws;
+            carve_uf(uc, fa, H, W);
             fa.in = Bs[i];
             fa.ld_in = W;
             fa.H = H;
             fa.W = W;
-            fa.U = U;
-            fa.A = A;
             uint8_t *F = t.filled ? t.filled : Fw;
             const int64_t ldF = t.filled ? t.ld_filled : W;
             {
                 Phase ph(ctx, RT_PHASE_FILL, s);
                 ctx->launches += 4;
                 RT_CUDA_TRY(uf_build(fa, P.conn_fill, kFgZero, false, true, s));
-                RT_CUDA_TRY(uf_fill_out(fa, F, ldF, s));
+                RT_CUDA_TRY(uf_fill_out(fa, P.conn_fill, F, ldF, s));
             }
             UfArgs la = fa;
             la.in = F;
@@ -584,7 +590,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
                 Phase ph(ctx, RT_PHASE_LABEL, s);
                 ctx->launches += 4;
                 RT_CUDA_TRY(uf_build(la, 8, kFgNonzero, true, false, s));
-                RT_CUDA_TRY(uf_labels_out(la, t.labels, t.ld_labels, P.min_area, P.max_area, t.n_kept, s));
+                RT_CUDA_TRY(uf_labels_out(la, 8, t.labels, t.ld_labels, P.min_area, P.max_area, t.n_kept, s));
             }
             EdtArgs ea;
             ea.fg8 = nullptr;

@@ -5,20 +5,34 @@
 // are read off by flattening the trees. Merging always hooks the root with
 // the larger linear index under the smaller one (atomicMin on the parent),
 // so the root of a finished tree is the smallest index of its component:
-// the canonical label. The forest is built in two levels:
-//   1. each 32 x 32 block merges its own pixels in shared memory and writes
-//      for every pixel the (global) index of its block-local root;
-//   2. pixel pairs that straddle a block edge are merged in global memory;
-//   3. flattening points every pixel at its final root and accumulates, per
-//      root, the component area (labeling) or whether the component touches
-//      the image border (hole filling: the background components are built
-//      and the ones that do not touch the border are holes).
+// the canonical label. The forest is built in two levels so that global
+// memory only ever holds the roots of block-local components:
+//   1. each 32 x 32 block labels its own pixels in shared memory; for every
+//      local root it records the local area (or whether the local component
+//      touches the image border) and appends the root to a list; for the
+//      pixels on the block's four edges it records their local root;
+//   2. local roots of pixels that touch across a block edge are merged in
+//      global memory (only those roots are nodes of the global forest);
+//   3. every listed local root is pointed at its final root, to which it adds
+//      its area (labeling) or its border flag (hole filling: the components
+//      are the background's, and those that never touch the border are the
+//      holes);
+//   4. the output pass labels each block again in shared memory (the local
+//      roots come out identical) and maps every pixel through its local
+//      root's final root.
 #include "ccl.cuh"
 
 namespace rtk {
 
-constexpr int kB = 32;          // block side
-constexpr int kRowsPerThread = 4;
+constexpr int kB = kUfBlock;
+constexpr int kRowsPerThread = 4;   // 256 threads: warp w owns rows 4w .. 4w+3
+
+size_t uf_workspace_bytes(int H, int W)
+{
+    const size_t N = (size_t)H * W;
+    const size_t nblk = (size_t)ceil_div(W, kB) * ceil_div(H, kB);
+    return 2 * N * sizeof(int32_t) + nblk * kUfEdge * sizeof(int32_t) + (N / 2 + 2) * sizeof(int32_t) + 8 * 256;
+}
 
 __device__ __forceinline__ bool is_fg(const uint8_t *in, int64_t ld, int r, int c, int source)
 {
@@ -70,21 +84,10 @@ __device__ __forceinline__ void union_s(int *P, int a, int b)
 }
 
 // ---------------------------------------------------- global forest
-__device__ __forceinline__ int32_t find_g(const int32_t *U, int32_t x)
-{
-    int32_t p = ld_relaxed_i32(U + x);
-    while (p != x) {
-        x = p;
-        p = ld_relaxed_i32(U + x);
-    }
-    return x;
-}
-
-// Path halving for the flatten pass (after every union is done). Other
-// threads store final roots into the same nodes meanwhile; since every
-// ancestor has a smaller index than its descendants and the root is the
-// smallest of all, the halving store is an atomicMin, so no node can move
-// back from its root to a lower ancestor.
+// Path halving. Every ancestor has a smaller index than its descendants, so
+// the halving store is an atomicMin: no node ever moves back from a higher
+// ancestor (or, once unions are over, from its final root, which other
+// threads store with plain writes) to a lower one.
 __device__ __forceinline__ int32_t find_g_halve(int32_t *U, int32_t x)
 {
     int32_t p = ld_relaxed_i32(U + x);
@@ -97,11 +100,13 @@ __device__ __forceinline__ int32_t find_g_halve(int32_t *U, int32_t x)
     return x;
 }
 
+// Hooking and halving are both atomicMin, so every parent only moves to a
+// smaller index in the same (growing) tree while unions run concurrently.
 __device__ __forceinline__ void union_g(int32_t *U, int32_t a, int32_t b)
 {
     for (;;) {
-        a = find_g(U, a);
-        b = find_g(U, b);
+        a = find_g_halve(U, a);
+        b = find_g_halve(U, b);
         if (a == b) return;
         if (a < b) {
             const int32_t t = a; a = b; b = t;
@@ -112,20 +117,20 @@ __device__ __forceinline__ void union_g(int32_t *U, int32_t a, int32_t b)
     }
 }
 
-// 1. block-local forests. Block of 32 x 32 pixels, 8 warps; warp w owns rows
-// 4w .. 4w+3 and lane = column. Inside a row, a run of foreground pixels
-// is one tree from the start: every pixel points at the run's first pixel
-// (found from the row's ballot mask). Rows are then joined with one union per
-// pair of touching runs: for 4-connectivity at the first column where the
-// runs overlap; for 8-connectivity the first pixel of a run joins each run of
-// the row above that starts within its three upper neighbours, and any other
-// pixel joins only a run of the row above that starts at its upper-right
-// neighbour.
+// ---------------------------------------------------- block-local labeling
+// Labels block (blockIdx.x, blockIdx.y) in shared memory. Inside a row, a run
+// of foreground pixels is one tree from the start: every pixel points at the
+// run's first pixel (found from the row's ballot mask). Rows are then joined
+// with one union per pair of touching runs: for 4-connectivity at the first
+// column where the runs overlap; for 8-connectivity the first pixel of a run
+// joins each run of the row above that starts within its three upper
+// neighbours, and any other pixel joins only a run of the row above that
+// starts at its upper-right neighbour. On return roots[k] holds the local
+// index (lr * 32 + c) of the root of the thread's k-th pixel, or -1.
 template <int CONN>
-__global__ void __launch_bounds__(256) uf_local_kernel(UfArgs a, int source, bool zero_acc)
+__device__ __forceinline__ void local_labels(const UfArgs &a, int source, int *P, uint32_t *M,
+                                             int roots[kRowsPerThread])
 {
-    __shared__ int P[kB * kB];
-    __shared__ uint32_t M[kB];
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
     const int c = c0 + tx;
@@ -168,154 +173,204 @@ __global__ void __launch_bounds__(256) uf_local_kernel(UfArgs a, int source, boo
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
+        const int i = (w * kRowsPerThread + k) * kB + tx;
+        roots[k] = P[i] >= 0 ? find_s_halve(P, i) : -1;
+    }
+}
+
+__device__ __forceinline__ int32_t global_index(const UfArgs &a, int local)
+{
+    const int r = blockIdx.y * kB + local / kB, c = blockIdx.x * kB + local % kB;
+    return (int32_t)((int64_t)r * a.W + c);
+}
+
+// 1. block-local components, their roots, areas / border flags and edges
+template <int CONN>
+__global__ void __launch_bounds__(256) uf_local_kernel(UfArgs a, int source, bool count_area)
+{
+    __shared__ int P[kB * kB];
+    __shared__ int cnt[kB * kB];
+    __shared__ uint32_t M[kB];
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kB * kB; i += blockDim.x) cnt[i] = 0;
+    int roots[kRowsPerThread];
+    local_labels<CONN>(a, source, P, M, roots);
+    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        if (roots[k] < 0) continue;
+        const int r = r0 + w * kRowsPerThread + k, c = c0 + tx;
+        if (count_area) atomicAdd(cnt + roots[k], 1);
+        else if (r == 0 || c == 0 || r == a.H - 1 || c == a.W - 1) cnt[roots[k]] = 1;
+    }
+    __syncthreads();
+    int32_t *edge = a.edge + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kUfEdge;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
         const int lr = w * kRowsPerThread + k;
-        const int r = r0 + lr;
         const int i = lr * kB + tx;
-        const int root = P[i] >= 0 ? find_s_halve(P, i) : -1;
-        if (r >= a.H || c >= a.W) continue;
-        const int64_t p = (int64_t)r * a.W + c;
-        int32_t g = -1;
-        if (root >= 0) {
-            g = (int32_t)((int64_t)(r0 + root / kB) * a.W + (c0 + root % kB));
-            if (zero_acc && root == i) a.A[p] = 0;
+        const int32_t g = roots[k] >= 0 ? global_index(a, roots[k]) : -1;
+        if (lr == 0) edge[tx] = g;
+        if (lr == kB - 1) edge[kB + tx] = g;
+        if (tx == 0) edge[2 * kB + lr] = g;
+        if (tx == kB - 1) edge[3 * kB + lr] = g;
+        const bool is_root = roots[k] == i;
+        if (is_root) {
+            a.U[g] = g;
+            a.A[g] = cnt[i];
         }
-        a.U[p] = g;
+        const unsigned rm = __ballot_sync(0xffffffffu, is_root);
+        if (rm) {
+            uint32_t base = 0;
+            const int leader = __ffs(rm) - 1;
+            if (tx == leader) base = atomicAdd(a.nlist, (uint32_t)__popc(rm));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (is_root) a.list[base + __popc(rm & ((1u << tx) - 1))] = g;
+        }
     }
 }
 
 // 2. merges across block edges, one CTA of 96 threads per block: threads
 // 0..31 the top row (with the row above), 32..63 the left column (with the
-// column to the left), 64..95 the right column (up-right neighbours, 8 only).
-// Pixels adjacent along the same block row or column are already in one
-// block-local tree, so along an edge only the first pixel pair of each pair
-// of touching runs needs a union; the others are skipped.
+// column to the left), 64..95 the right column (up-right neighbours, 8
+// only). The nodes are the local roots recorded on the block edges. Pixels
+// adjacent along one block row or column already share a local root, so
+// along an edge only the first pixel pair of each pair of touching runs
+// needs a union; the others are skipped.
 template <int CONN>
-__global__ void __launch_bounds__(96) uf_border_kernel(UfArgs a, int source)
+__global__ void __launch_bounds__(96) uf_border_kernel(UfArgs a)
 {
-    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
+    const int bx = blockIdx.x, by = blockIdx.y, nbx = gridDim.x;
     const int pos = threadIdx.x;
-    auto fg = [&](int r, int c) { return r >= 0 && c >= 0 && r < a.H && c < a.W && is_fg(a.in, a.ld_in, r, c, source); };
+    auto E = [&](int x, int y) -> const int32_t * { return a.edge + ((int64_t)y * nbx + x) * kUfEdge; };
+    const int32_t *me = E(bx, by);
     if (pos < 32) {
-        const int r = r0, c = c0 + pos;
-        if (r == 0 || c >= a.W || !fg(r, c)) return;
-        const int32_t p = (int32_t)((int64_t)r * a.W + c);
-        const bool left_in = pos > 0 && fg(r, c - 1);          // same block row
-        const bool right_in = pos < 31 && fg(r, c + 1);
-        if (fg(r - 1, c) && !(left_in && fg(r - 1, c - 1))) union_g(a.U, p, p - a.W);
+        if (by == 0) return;
+        const int k = pos;
+        const int32_t p = me[k];
+        if (p < 0) return;
+        const int32_t *ab = E(bx, by - 1) + kB;          // bottom row of the block above
+        const bool left_in = k > 0 && me[k - 1] >= 0;
+        const bool right_in = k < kB - 1 && me[k + 1] >= 0;
+        if (ab[k] >= 0 && !(left_in && ab[k - 1] >= 0)) union_g(a.U, p, ab[k]);
         if (CONN == 8) {
-            if (c > 0 && fg(r - 1, c - 1) && !left_in) union_g(a.U, p, p - a.W - 1);
-            if (fg(r - 1, c + 1) && !right_in) union_g(a.U, p, p - a.W + 1);
+            const int32_t ul = k > 0 ? ab[k - 1] : (bx > 0 ? E(bx - 1, by - 1)[kB + kB - 1] : -1);
+            const int32_t ur = k < kB - 1 ? ab[k + 1] : (bx + 1 < nbx ? E(bx + 1, by - 1)[kB] : -1);
+            if (ul >= 0 && !left_in) union_g(a.U, p, ul);
+            if (ur >= 0 && !right_in) union_g(a.U, p, ur);
         }
     } else if (pos < 64) {
-        const int r = r0 + pos - 32, c = c0;
-        if (c == 0 || r >= a.H || !fg(r, c)) return;
-        const int32_t p = (int32_t)((int64_t)r * a.W + c);
-        const bool up_in = r > r0 && fg(r - 1, c);              // same block column
-        if (fg(r, c - 1) && !(up_in && fg(r - 1, c - 1))) union_g(a.U, p, p - 1);
-        if (CONN == 8 && r > r0 && fg(r - 1, c - 1) && !up_in) union_g(a.U, p, p - a.W - 1);
+        if (bx == 0) return;
+        const int k = pos - 32;
+        const int32_t p = me[2 * kB + k];
+        if (p < 0) return;
+        const int32_t *lr = E(bx - 1, by) + 3 * kB;      // right column of the block to the left
+        const bool up_in = k > 0 && me[2 * kB + k - 1] >= 0;
+        if (lr[k] >= 0 && !(up_in && lr[k - 1] >= 0)) union_g(a.U, p, lr[k]);
+        if (CONN == 8 && k > 0 && lr[k - 1] >= 0 && !up_in) union_g(a.U, p, lr[k - 1]);
     } else {
-        if (CONN != 8) return;
-        const int r = r0 + pos - 64, c = c0 + kB - 1;
-        if (r == r0 || r >= a.H || c + 1 >= a.W || !fg(r, c)) return;
-        const int32_t p = (int32_t)((int64_t)r * a.W + c);
-        if (fg(r - 1, c + 1) && !fg(r - 1, c)) union_g(a.U, p, p - a.W + 1);
+        if (CONN != 8 || bx + 1 >= nbx) return;
+        const int k = pos - 64;
+        if (k == 0) return;                              // handled as a top-row pixel
+        const int32_t p = me[3 * kB + k];
+        if (p < 0) return;
+        const int32_t q = E(bx + 1, by)[2 * kB + k - 1];  // left column of the block to the right, row above
+        if (q >= 0 && me[3 * kB + k - 1] < 0) union_g(a.U, p, q);
     }
 }
 
-// 3. flatten: U[p] = root(p); accumulate area (warp-aggregated) or the
-// border flag at the root.
-__global__ void uf_flatten_kernel(UfArgs a, bool count_area, bool flag_border)
+// 3. final roots of the local roots, with areas or border flags
+__global__ void uf_roots_kernel(UfArgs a, bool count_area)
 {
-    const int r = blockIdx.y;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c - (int)threadIdx.x < a.W; c += gridDim.x * blockDim.x) {
-        const bool in = c < a.W;
-        const int64_t p = (int64_t)r * a.W + c;
-        int32_t root = -1;
-        const int32_t u = in ? a.U[p] : -1;
-        // lanes holding the same value share one find
-        const unsigned has = __ballot_sync(0xffffffffu, u >= 0);
-        if (u >= 0) {
-            const unsigned same = __match_any_sync(has, u);
-            const int leader = __ffs(same) - 1;
-            if ((int)(threadIdx.x & 31) == leader) root = find_g_halve(a.U, u);
-            root = __shfl_sync(same, root, leader);
-            // plain store: the root is the smallest value any concurrent
-            // halving (atomicMin) could write here
-            if (root != u) a.U[p] = root;
-        }
-        if (count_area) {
-            const unsigned act = __ballot_sync(0xffffffffu, root >= 0);
-            if (root >= 0) {
-                const unsigned peers = __match_any_sync(act, root);
-                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.A + root, __popc(peers));
-            }
-        }
-        if (flag_border && root >= 0 && (r == 0 || r == a.H - 1 || c == 0 || c == a.W - 1)) a.A[root] = 1;
+    const uint32_t n = *a.nlist;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t L = a.list[i];
+        const int32_t root = find_g_halve(a.U, L);
+        if (root == L) continue;
+        a.U[L] = root;     // plain store: no concurrent value can be smaller
+        if (count_area) atomicAdd(a.A + root, a.A[L]);
+        else if (a.A[L]) a.A[root] = 1;
     }
 }
 
 cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, bool flag_border, cudaStream_t s)
 {
+    (void)flag_border;
     const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
-    const bool zero = count_area || flag_border;
-    if (conn == 8) uf_local_kernel<8><<<grid_blk, 256, 0, s>>>(a, source, zero);
-    else uf_local_kernel<4><<<grid_blk, 256, 0, s>>>(a, source, zero);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(a.nlist, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    if (conn == 8) uf_border_kernel<8><<<grid_blk, 96, 0, s>>>(a, source);
-    else uf_border_kernel<4><<<grid_blk, 96, 0, s>>>(a, source);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int bx = (int)ceil_div(a.W, 256);
-    uf_flatten_kernel<<<dim3((unsigned)bx, (unsigned)a.H), 256, 0, s>>>(a, count_area, flag_border);
+    if (conn == 8) uf_local_kernel<8><<<grid_blk, 256, 0, s>>>(a, source, count_area);
+    else uf_local_kernel<4><<<grid_blk, 256, 0, s>>>(a, source, count_area);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (conn == 8) uf_border_kernel<8><<<grid_blk, 96, 0, s>>>(a);
+    else uf_border_kernel<4><<<grid_blk, 96, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    uf_roots_kernel<<<1024, 256, 0, s>>>(a, count_area);
     return cudaGetLastError();
 }
 
 // 4a. labels with the area filter
-__global__ void uf_labels_kernel(UfArgs a, int32_t *labels, int64_t ld_lab, int32_t amin, int32_t amax,
-                                 int32_t *n_kept)
+template <int CONN>
+__global__ void __launch_bounds__(256) uf_labels_kernel(UfArgs a, int32_t *labels, int64_t ld_lab, int32_t amin,
+                                                        int32_t amax, int32_t *n_kept)
 {
-    const int r = blockIdx.y;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.W; c += gridDim.x * blockDim.x) {
-        const int64_t p = (int64_t)r * a.W + c;
-        const int32_t root = a.U[p];
+    __shared__ int P[kB * kB];
+    __shared__ uint32_t M[kB];
+    int roots[kRowsPerThread];
+    local_labels<CONN>(a, kFgNonzero, P, M, roots);
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB, c = c0 + tx;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        const int r = r0 + w * kRowsPerThread + k;
+        if (r >= a.H || c >= a.W) continue;
         int32_t out = -1;
-        if (root >= 0) {
+        if (roots[k] >= 0) {
+            const int32_t root = a.U[global_index(a, roots[k])];
             const int32_t area = a.A[root];
             if (area >= amin && area <= amax) {
                 out = root;
-                if (root == p && n_kept) atomicAdd(n_kept, 1);
+                if (n_kept && root == (int32_t)((int64_t)r * a.W + c)) atomicAdd(n_kept, 1);
             }
         }
         labels[(int64_t)r * ld_lab + c] = out;
     }
 }
 
-cudaError_t uf_labels_out(const UfArgs &a, int32_t *labels, int64_t ld_lab, int32_t min_area,
+cudaError_t uf_labels_out(const UfArgs &a, int conn, int32_t *labels, int64_t ld_lab, int32_t min_area,
                           int32_t max_area, int32_t *n_kept, cudaStream_t s)
 {
-    const int bx = (int)ceil_div(a.W, 256);
-    uf_labels_kernel<<<dim3((unsigned)bx, (unsigned)a.H), 256, 0, s>>>(a, labels, ld_lab, min_area, max_area,
-                                                                       n_kept);
+    const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
+    if (conn == 8) uf_labels_kernel<8><<<grid_blk, 256, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
+    else uf_labels_kernel<4><<<grid_blk, 256, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
     return cudaGetLastError();
 }
 
 // 4b. hole filling from the background components
-__global__ void uf_fill_kernel(UfArgs a, uint8_t *out, int64_t ld_out)
+template <int CONN>
+__global__ void __launch_bounds__(256) uf_fill_kernel(UfArgs a, uint8_t *out, int64_t ld_out)
 {
-    const int r = blockIdx.y;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.W; c += gridDim.x * blockDim.x) {
-        const int64_t p = (int64_t)r * a.W + c;
-        const int32_t root = a.U[p];     // background pixels have a root
-        const uint8_t v = (root < 0) ? 1 : (a.A[root] ? 0 : 1);
+    __shared__ int P[kB * kB];
+    __shared__ uint32_t M[kB];
+    int roots[kRowsPerThread];
+    local_labels<CONN>(a, kFgZero, P, M, roots);
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB, c = c0 + tx;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        const int r = r0 + w * kRowsPerThread + k;
+        if (r >= a.H || c >= a.W) continue;
+        uint8_t v = 1;   // foreground
+        if (roots[k] >= 0) v = a.A[a.U[global_index(a, roots[k])]] ? 0 : 1;
         out[(int64_t)r * ld_out + c] = v;
     }
 }
 
-cudaError_t uf_fill_out(const UfArgs &a, uint8_t *out, int64_t ld_out, cudaStream_t s)
+cudaError_t uf_fill_out(const UfArgs &a, int conn, uint8_t *out, int64_t ld_out, cudaStream_t s)
 {
-    const int bx = (int)ceil_div(a.W, 256);
-    uf_fill_kernel<<<dim3((unsigned)bx, (unsigned)a.H), 256, 0, s>>>(a, out, ld_out);
+    const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
+    if (conn == 8) uf_fill_kernel<8><<<grid_blk, 256, 0, s>>>(a, out, ld_out);
+    else uf_fill_kernel<4><<<grid_blk, 256, 0, s>>>(a, out, ld_out);
     return cudaGetLastError();
 }
 

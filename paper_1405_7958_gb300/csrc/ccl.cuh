@@ -9,20 +9,33 @@ namespace rtk {
 // (background components, used by hole filling).
 enum UfSource { kFgNonzero = 0, kFgZero = 1 };
 
+constexpr int kUfBlock = 32;       // block side
+constexpr int kUfEdge = 4 * kUfBlock;
+
 struct UfArgs {
     const uint8_t *in;   // binary input, H x W, stride ld_in
     int64_t ld_in;
     int H, W;
-    int32_t *U;          // parent forest, H*W int32, index r*W + c (workspace)
-    int32_t *A;          // per-root accumulator (area or border flag), H*W int32 (workspace)
+    int32_t *U;          // forest over block-local roots, indexed by pixel index r*W + c (sparse use)
+    int32_t *A;          // per local root: area or border flag (sparse use)
+    int32_t *edge;       // per block, kUfEdge entries: local root of the top row, bottom row,
+                         // left column, right column pixels (-1 = not in a component)
+    int32_t *list;       // the local roots
+    uint32_t *nlist;     // their number
 };
 
+// Workspace bytes the four arrays need for an H x W image.
+size_t uf_workspace_bytes(int H, int W);
+
+// Builds the forest: block-local components, merges across block edges, and
+// the final root of every local root with its aggregated area (count_area)
+// or border-contact flag (flag_border).
 cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, bool flag_border,
                      cudaStream_t s);
 // labels = root if fg and min_area <= area(root) <= max_area, else -1
-cudaError_t uf_labels_out(const UfArgs &a, int32_t *labels, int64_t ld_lab, int32_t min_area,
+cudaError_t uf_labels_out(const UfArgs &a, int conn, int32_t *labels, int64_t ld_lab, int32_t min_area,
                           int32_t max_area, int32_t *n_kept, cudaStream_t s);
 // out = 1 where in != 0 or the background component does not touch the border
-cudaError_t uf_fill_out(const UfArgs &a, uint8_t *out, int64_t ld_out, cudaStream_t s);
+cudaError_t uf_fill_out(const UfArgs &a, int conn, uint8_t *out, int64_t ld_out, cudaStream_t s);
 
 }  // namespace rtk
