@@ -36,7 +36,7 @@ BYTES_RECON = 2          # reconstruction: read mask 1, write R 1
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8, help="tiles per step per GPU")
     ap.add_argument("--size", type=int, default=4096)
@@ -86,7 +86,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
@@ -95,7 +95,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def window(self, t0, t1):
+        """Keep only samples that arrived during [t0, t1] (wall clock)."""
+        self.t0, self.t1 = t0, t1
 
     def stop(self):
         if self.proc is None:
@@ -109,7 +113,10 @@ class ClockSampler:
             self.thread.join(timeout=2)
         mhz, maxes, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        t0, t1 = getattr(self, "t0", 0.0), getattr(self, "t1", float("inf"))
+        for ts, ln in self.lines:
+            if ts < t0 or ts > t1 + 0.25:
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -192,6 +199,8 @@ def run_native(a, rank, world, local_rank):
     params = rt.SegParams()
     stream = torch.cuda.current_stream()
     imgs = [torch.from_numpy(t).to(dev) for t in tiles]
+    sampler = ClockSampler(local_rank)
+    sampler.start()
     outs = None
     for _ in range(a.warmup):
         outs = rt.segment_batch(imgs, params, outputs=outs, ctx=ctx)
@@ -201,16 +210,16 @@ def run_native(a, rank, world, local_rank):
     ctx.timing(True)
     ctx.read_timing(reset=True)
     l0 = ctx.kernel_launches()
-    sampler = ClockSampler(local_rank)
-    sampler.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     barrier()
+    wall0 = time.time()
     for k in range(a.steps):
         flush.fill_(k & 0xFF)
         evs[k][0].record(stream)
         outs = rt.segment_batch(imgs, params, outputs=outs, ctx=ctx)
         evs[k][1].record(stream)
     barrier()
+    sampler.window(wall0, time.time())
     clocks = sampler.stop()
     launches = ctx.kernel_launches() - l0
     step_ms = [s.elapsed_time(e) for s, e in evs]

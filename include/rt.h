@@ -170,7 +170,8 @@ enum {
     RT_PHASE_FILL = 3,         /* hole filling */
     RT_PHASE_LABEL = 4,        /* labeling and area filter */
     RT_PHASE_EDT = 5,          /* distance transform */
-    RT_NPHASES = 6
+    RT_PHASE_PICK = 6,         /* features and picker network */
+    RT_NPHASES = 7
 };
 
 /*
@@ -210,6 +211,83 @@ RT_API rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iteration
 RT_API rt_status rt_edt_noalloc(const uint8_t *fg, int64_t ld_fg, int32_t *d2, int64_t ld_d2,
                                 int H, int W, int32_t *dev_status, void *stream);
 
+/*
+ * Seeded synthetic nuclei tile, drawn on the GPU (input generation, not an
+ * operation of the paper). The paper evaluates on 4K x 4K tiles of
+ * brain-tumour slides (Section 5); this generator makes stand-ins of the
+ * same size: dark ellipses (kind 0; semi-axes amin..amax px) or disks
+ * (kind 1; radii rmin..rmax px) with intensities vlo..vhi on a 200 +- 15
+ * lattice-noise background (flat = 1: constant 200), plus integer noise of
+ * standard deviation ~8 (noise = 1). Every draw comes from Philox4x32-10 and
+ * all geometry is integer, so the bytes equal those of the project's Python
+ * generator for the same parameters. out: uint8 H x W (ld).
+ */
+RT_API rt_status rt_synth_tile(rt_ctx *ctx, uint8_t *out, int64_t ld, int H, int W, uint64_t seed,
+                               int n_shapes, int kind, int vlo, int vhi, int rmin, int rmax,
+                               int amin, int amax, int flat, int noise, void *stream);
+
+/*
+ * Learned variant picker. The paper's PATS scheduler (Section 3.2.1) orders
+ * tasks by estimated speedup because the run time of its irregular
+ * operations cannot be estimated in advance; here a small network reads 24
+ * cheap statistics of a tile and picks the propagation variant of its
+ * reconstruction (RT_RASTER, RT_QUEUE or RT_HYBRID, class index = variant - 1).
+ *
+ * rt_tile_features: features of n tiles (host arrays of device pointers,
+ * strides and sizes; n <= 32) into out, a device float array n x
+ * RT_NFEATURES, row-major. The features, in order: H, W, ln(H W); mean,
+ * variance, skewness, kurtosis of the histogram; the lower 1, 5, 10, 25, 50,
+ * 75, 90, 95, 99 percentiles; the fractions below 80 and below 110; the
+ * histogram entropy (bits); mean and population standard deviation over 8 x 8
+ * blocks of the fraction of pixels below 80, and the fraction of blocks above
+ * 0.1; on the 8 x 8 block maximum D with marker max(D - 30, 0) (D on its
+ * border), the fraction of pixels a raster-order neighbour could raise, and
+ * ln(1 + their count).
+ */
+#define RT_NFEATURES 24
+#define RT_MLP_NPARAM 5955
+RT_API rt_status rt_tile_features(rt_ctx *ctx, const uint8_t *const *imgs, const int64_t *lds,
+                                  const int *Hs, const int *Ws, int n, float *out, void *stream);
+
+/*
+ * The network: 24 -> 64 -> 64 -> 3, ReLU, bf16 parameters, fp32
+ * accumulation. Parameters are one flat vector of RT_MLP_NPARAM values,
+ * W1[64][24] b1[64] W2[64][64] b2[64] W3[3][64] b3[3] (row-major), as bf16
+ * bit patterns (wb) for compute and fp32 (master) for the optimizer. norm
+ * holds mu[24] then sd[24]; the input is normalised as (x - mu) / sd. All
+ * pointers are device pointers.
+ *
+ * rt_mlp_forward: logits (B x 3, nullable), saved activations act (B x 128:
+ * h1 then h2 after ReLU, nullable, needed by the backward pass) and the
+ * argmax pick (B int32, nullable).
+ * rt_mlp_backward: gradient of the mean cross-entropy loss with respect to
+ * every parameter into grad (RT_MLP_NPARAM fp32, overwritten), and the loss
+ * into *loss (device float, nullable); label holds class indices 0..2. The
+ * batch sums run in a fixed order, so the result is deterministic.
+ * rt_mlp_adamw: one AdamW step (step counts from 1) on master, then wb =
+ * bf16(master) with round-to-nearest-even; m and v are the moment buffers.
+ */
+RT_API rt_status rt_mlp_forward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, int B,
+                                float *logits, float *act, int32_t *pick, void *stream);
+RT_API rt_status rt_mlp_backward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x,
+                                 const float *act, const float *logits, const int32_t *label, int B,
+                                 float *grad, float *loss, void *stream);
+RT_API rt_status rt_mlp_adamw(rt_ctx *ctx, float *master, uint16_t *wb, const float *grad, float *m,
+                              float *v, int step, float lr, float beta1, float beta2, float eps,
+                              float weight_decay, void *stream);
+
+/*
+ * Attach a trained picker (device pointers, owned by the caller and read
+ * during later calls) to the context for rt_segment_batch with
+ * policy = RT_POLICY_LEARNED; NULL detaches it.
+ */
+RT_API rt_status rt_set_picker(rt_ctx *ctx, const uint16_t *wb, const float *norm);
+
+/* Variants (RT_RASTER..RT_HYBRID) the picker chose for the tiles of the last
+ * chunk (up to 32 tiles) of the last learned rt_segment_batch call; copies up
+ * to cap of them into variants (nullable) and returns how many there were. */
+RT_API int rt_last_picks(const rt_ctx *ctx, int *variants, int cap);
+
 /* One tile of a batch. Every pointer is a device pointer. */
 typedef struct {
     const uint8_t *img;   /* input tile I, uint8 H x W */
@@ -237,9 +315,14 @@ typedef struct {
     int conn_fill;   /* connectivity of the background flood in fill-holes (4) */
     int variant;     /* reconstruction variant for every tile (RT_AUTO) */
     int max_local;   /* sweep iterations per dense tile visit; 0 = default */
+    int policy;      /* RT_POLICY_PLAIN: `variant` for every tile;
+                        RT_POLICY_LEARNED: the attached picker chooses per tile and the
+                        plain choice is kept whenever no picker is attached */
 } rt_seg_params;
 
-/* Fill `p` with the defaults listed above. */
+enum { RT_POLICY_PLAIN = 0, RT_POLICY_LEARNED = 1 };
+
+/* Fill `p` with the defaults listed above (policy RT_POLICY_PLAIN). */
 RT_API void rt_seg_params_default(rt_seg_params *p);
 
 /*

@@ -188,6 +188,129 @@ def edt(fg: torch.Tensor, *, out=None, status=None, ctx=None, stream=None):
     return out
 
 
+def synth_tile(H: int, W: int, seed: int, n_shapes: int, *, kind: str = "ellipse", vlo: int = 30, vhi: int = 100,
+               rmin: int = 4, rmax: int = 12, amin: int = 4, amax: int = 14, background: str = "perlin",
+               noise: bool = True, out=None, device=None, ctx=None, stream=None) -> torch.Tensor:
+    """Seeded nuclei tile drawn on the GPU; same bytes as synth.tile() with
+    the same arguments."""
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    ctx = ctx or default_context(torch.device(device).index)
+    out = torch.empty((H, W), dtype=torch.uint8, device=device) if out is None else out
+    op, old = _dev_ptr(out, torch.uint8, "out")
+    _check(lib().rt_synth_tile(ctx.handle, op, old, H, W, int(seed), int(n_shapes), 1 if kind == "disk" else 0,
+                               vlo, vhi, rmin, rmax, amin, amax, 1 if background == "flat" else 0, int(bool(noise)),
+                               _stream(stream)), "rt_synth_tile")
+    return out
+
+
+def config2_tile(seed: int = 2000, H: int = 4096, W: int = 4096, n_shapes: int | None = None, **kw):
+    """GPU twin of synth.config2_tile."""
+    if n_shapes is None:
+        n_shapes = int(round(3000 * H * W / (4096 * 4096)))
+    return synth_tile(H, W, seed, n_shapes, kind="ellipse", vlo=30, vhi=100, **kw)
+
+
+def tile_features(images, *, out=None, ctx=None, stream=None) -> torch.Tensor:
+    """The picker's 24 features of each uint8 CUDA tile (n <= 32 per call
+    chunk; longer lists are processed in chunks). Returns float32 n x 24."""
+    if not images:
+        return torch.empty((0, _native.RT_NFEATURES), dtype=torch.float32)
+    ctx = ctx or default_context(images[0].device.index)
+    n = len(images)
+    out = torch.empty((n, _native.RT_NFEATURES), dtype=torch.float32, device=images[0].device) if out is None else out
+    for c0 in range(0, n, 32):
+        chunk = images[c0:c0 + 32]
+        m = len(chunk)
+        ptrs = (ctypes.c_void_p * m)()
+        lds = (ctypes.c_int64 * m)()
+        hs = (ctypes.c_int * m)()
+        ws = (ctypes.c_int * m)()
+        for i, img in enumerate(chunk):
+            ptrs[i], lds[i] = _dev_ptr(img, torch.uint8, "image")
+            hs[i], ws[i] = img.shape
+        _check(lib().rt_tile_features(ctx.handle, ptrs, lds, hs, ws, m, out[c0:].data_ptr(), _stream(stream)),
+               "rt_tile_features")
+    return out
+
+
+class Picker:
+    """The learned variant picker: parameters on the GPU (bf16 working copy,
+    fp32 master, AdamW moments) and the normalisation of the features. Every
+    computation runs in the library's kernels."""
+
+    NPARAM = _native.RT_MLP_NPARAM
+
+    def __init__(self, device=None, seed: int = 0, norm=None, ctx=None):
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        self.ctx = ctx or default_context(self.device.index)
+        g = torch.Generator().manual_seed(seed)
+        # He-style initial weights (drawn on the host once), zero biases
+        p = torch.zeros(self.NPARAM, dtype=torch.float32)
+        p[0:1536] = torch.randn(1536, generator=g) * (2.0 / 24) ** 0.5
+        p[1600:5696] = torch.randn(4096, generator=g) * (2.0 / 64) ** 0.5
+        p[5760:5952] = torch.randn(192, generator=g) * (1.0 / 64) ** 0.5
+        self.master = p.to(self.device)
+        self.wb = self.master.to(torch.bfloat16).view(torch.int16).contiguous()
+        self.m = torch.zeros_like(self.master)
+        self.v = torch.zeros_like(self.master)
+        self.grad = torch.zeros_like(self.master)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.norm = torch.cat([torch.zeros(24), torch.ones(24)]).to(self.device) if norm is None else norm
+        self.step_count = 0
+
+    def set_norm(self, feats: torch.Tensor):
+        mu = feats.mean(dim=0)
+        sd = feats.std(dim=0).clamp_min(1e-6)
+        self.norm = torch.cat([mu, sd]).float().contiguous().to(self.device)
+
+    def forward(self, x: torch.Tensor, with_act: bool = False, stream=None):
+        B = x.shape[0]
+        logits = torch.empty((B, 3), dtype=torch.float32, device=self.device)
+        act = torch.empty((B, 128), dtype=torch.float32, device=self.device) if with_act else None
+        pick = torch.empty(B, dtype=torch.int32, device=self.device)
+        _check(lib().rt_mlp_forward(self.ctx.handle, self.wb.data_ptr(), self.norm.data_ptr(), x.contiguous().data_ptr(),
+                                    B, logits.data_ptr(), None if act is None else act.data_ptr(), pick.data_ptr(),
+                                    _stream(stream)), "rt_mlp_forward")
+        return logits, act, pick
+
+    def backward(self, x, act, logits, label, stream=None):
+        _check(lib().rt_mlp_backward(self.ctx.handle, self.wb.data_ptr(), self.norm.data_ptr(), x.contiguous().data_ptr(),
+                                     act.data_ptr(), logits.data_ptr(), label.to(torch.int32).contiguous().data_ptr(),
+                                     x.shape[0], self.grad.data_ptr(), self.loss.data_ptr(), _stream(stream)),
+               "rt_mlp_backward")
+        return self.grad, self.loss
+
+    def step(self, lr=3e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4, stream=None):
+        self.step_count += 1
+        _check(lib().rt_mlp_adamw(self.ctx.handle, self.master.data_ptr(), self.wb.data_ptr(), self.grad.data_ptr(),
+                                  self.m.data_ptr(), self.v.data_ptr(), self.step_count, lr, beta1, beta2, eps,
+                                  weight_decay, _stream(stream)), "rt_mlp_adamw")
+
+    def attach(self, ctx=None):
+        """Use this picker in rt_segment_batch(policy=learned) on ctx."""
+        ctx = ctx or self.ctx
+        _check(lib().rt_set_picker(ctx.handle, self.wb.data_ptr(), self.norm.data_ptr()), "rt_set_picker")
+
+    def state_dict(self) -> dict:
+        return {k: getattr(self, k).detach().cpu() for k in ("master", "wb", "m", "v", "norm")} | {
+            "step_count": self.step_count}
+
+    def load_state_dict(self, sd: dict):
+        for k in ("master", "wb", "m", "v", "norm"):
+            setattr(self, k, sd[k].to(self.device).contiguous())
+        self.step_count = int(sd["step_count"])
+
+
+def last_picks(ctx=None) -> list:
+    ctx = ctx or default_context()
+    buf = (ctypes.c_int * 32)()
+    n = lib().rt_last_picks(ctx.handle, buf, 32)
+    return [buf[i] for i in range(min(n, 32))]
+
+
 @dataclass
 class SegParams:
     h_offset: int = 30
@@ -198,6 +321,7 @@ class SegParams:
     conn_fill: int = 4
     variant: int = RT_AUTO
     max_local: int = 0
+    policy: int = 0          # 0 plain (fixed variant), 1 learned (attached picker)
 
     def to_c(self) -> _native.RtSegParams:
         p = _native.RtSegParams()

@@ -18,10 +18,14 @@ EXPORTS = (
     "rt_create", "rt_destroy", "rt_status_str", "rt_version", "rt_workspace_bytes", "rt_marker",
     "rt_reconstruct", "rt_fill_holes", "rt_label_area", "rt_edt", "rt_seg_params_default",
     "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_recon_stats",
-    "rt_edt_noalloc",
+    "rt_edt_noalloc", "rt_synth_tile", "rt_tile_features", "rt_mlp_forward", "rt_mlp_backward",
+    "rt_mlp_adamw", "rt_set_picker", "rt_last_picks",
 )
-RT_NPHASES = 6
-PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt")
+RT_NPHASES = 7
+PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt", "pick")
+RT_NFEATURES = 24
+RT_MLP_NPARAM = 5955
+RT_POLICY_PLAIN, RT_POLICY_LEARNED = 0, 1
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -42,7 +46,7 @@ class RtTile(ctypes.Structure):
 
 class RtSegParams(ctypes.Structure):
     _fields_ = [(n, _int) for n in ("h_offset", "threshold", "min_area", "max_area", "conn_recon",
-                                    "conn_fill", "variant", "max_local")]
+                                    "conn_fill", "variant", "max_local", "policy")]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -71,6 +75,22 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_edt.restype = _int
     lib.rt_edt_noalloc.argtypes = [_vp, _i64, _vp, _i64, _int, _int, _vp, _vp]
     lib.rt_edt_noalloc.restype = _int
+    lib.rt_synth_tile.argtypes = [_vp, _vp, _i64, _int, _int, ctypes.c_uint64] + [_int] * 10 + [_vp]
+    lib.rt_synth_tile.restype = _int
+    lib.rt_tile_features.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_int),
+                                     ctypes.POINTER(_int), _int, _vp, _vp]
+    lib.rt_tile_features.restype = _int
+    lib.rt_mlp_forward.argtypes = [_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp]
+    lib.rt_mlp_forward.restype = _int
+    lib.rt_mlp_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp]
+    lib.rt_mlp_backward.restype = _int
+    _f = ctypes.c_float
+    lib.rt_mlp_adamw.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _int, _f, _f, _f, _f, _f, _vp]
+    lib.rt_mlp_adamw.restype = _int
+    lib.rt_set_picker.argtypes = [_vp, _vp, _vp]
+    lib.rt_set_picker.restype = _int
+    lib.rt_last_picks.argtypes = [_vp, ctypes.POINTER(_int), _int]
+    lib.rt_last_picks.restype = _int
     lib.rt_seg_params_default.argtypes = [ctypes.POINTER(RtSegParams)]
     lib.rt_seg_params_default.restype = None
     lib.rt_segment_batch.argtypes = [_vp, ctypes.POINTER(RtTile), _int, ctypes.POINTER(RtSegParams), _vp]

@@ -9,7 +9,10 @@
 #include "ccl.cuh"
 #include "common.cuh"
 #include "edt.cuh"
+#include "features.cuh"
+#include "mlp.cuh"
 #include "recon.cuh"
+#include "synth.cuh"
 
 using namespace rtk;
 
@@ -26,6 +29,10 @@ struct rt_ctx {
     uint32_t *visits_dev = nullptr;  // [visits, iterations] of the last reconstruction (workspace)
     int64_t launches = 0;     // kernels launched
     bool timing = false;
+    const uint16_t *picker_wb = nullptr;   // attached picker (caller-owned device memory)
+    const float *picker_norm = nullptr;
+    int last_picks[kMaxImgs] = {};          // variants the picker chose in the last chunk
+    int n_last_picks = 0;
     std::vector<PhaseRec> recs;
     std::vector<cudaEvent_t> pool;
 };
@@ -483,6 +490,115 @@ rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int
     return cuda_status(launch_edt(a, s));
 }
 
+rt_status rt_synth_tile(rt_ctx *ctx, uint8_t *out, int64_t ld, int H, int W, uint64_t seed, int n_shapes, int kind,
+                        int vlo, int vhi, int rmin, int rmax, int amin, int amax, int flat, int noise, void *stream)
+{
+    if (!ctx || !out || bad_dims(H, W) || ld < W || n_shapes < 0 || (kind != 0 && kind != 1)) return RT_EINVAL;
+    if (vlo < 0 || vhi > 255 || vlo > vhi || rmin < 0 || rmax < rmin || amin < 0 || amax < amin) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    rt_status st = ensure_ws(ctx, synth_workspace_bytes(H, W));
+    if (st != RT_OK) return st;
+    SynthArgs a;
+    a.H = H;
+    a.W = W;
+    a.k0 = (uint32_t)(seed & 0xffffffffu);
+    a.k1 = (uint32_t)(seed >> 32);
+    a.n_shapes = n_shapes;
+    a.kind = kind;
+    a.vlo = vlo;
+    a.vhi = vhi;
+    a.rmin = rmin;
+    a.rmax = rmax;
+    a.amin = amin;
+    a.amax = amax;
+    a.flat = flat != 0;
+    a.noise = noise != 0;
+    ctx->launches += 3;
+    return cuda_status(launch_synth(a, ctx->ws, out, ld, s));
+}
+
+rt_status rt_tile_features(rt_ctx *ctx, const uint8_t *const *imgs, const int64_t *lds, const int *Hs, const int *Ws,
+                           int n, float *out, void *stream)
+{
+    if (!ctx || !imgs || !lds || !Hs || !Ws || !out || n < 1 || n > kMaxFeatImgs) return RT_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!imgs[i] || bad_dims(Hs[i], Ws[i]) || lds[i] < Ws[i]) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    auto layout = [&](Carve &cv, FeatBatch &fb) {
+        fb.n = n;
+        for (int i = 0; i < n; ++i) {
+            const size_t nb = (size_t)((Hs[i] + 7) / 8) * ((Ws[i] + 7) / 8);
+            FeatImage &d = fb.img[i];
+            d.img = imgs[i];
+            d.ld = lds[i];
+            d.H = Hs[i];
+            d.W = Ws[i];
+            d.hist = cv.take<uint32_t>(256);
+            d.dark = cv.take<uint8_t>(nb);
+            d.bmax = cv.take<uint8_t>(nb);
+        }
+    };
+    FeatBatch fb;
+    Carve cv;
+    layout(cv, fb);
+    rt_status st = ensure_ws(ctx, cv.off);
+    if (st != RT_OK) return st;
+    cv = Carve();
+    cv.base = (char *)ctx->ws;
+    layout(cv, fb);
+    ctx->launches += 2;
+    return cuda_status(launch_features(fb, out, s));
+}
+
+rt_status rt_mlp_forward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, int B, float *logits,
+                         float *act, int32_t *pick, void *stream)
+{
+    if (!ctx || !wb || !norm || !x || B < 1) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    ctx->launches += 1;
+    return cuda_status(launch_mlp_forward(wb, norm, x, B, logits, act, pick, (cudaStream_t)stream));
+}
+
+rt_status rt_mlp_backward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, const float *act,
+                          const float *logits, const int32_t *label, int B, float *grad, float *loss, void *stream)
+{
+    if (!ctx || !wb || !norm || !x || !act || !logits || !label || !grad || B < 1) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    rt_status st = ensure_ws(ctx, mlp_backward_workspace_bytes(B));
+    if (st != RT_OK) return st;
+    ctx->launches += 2;
+    return cuda_status(launch_mlp_backward(wb, norm, x, act, logits, label, B, grad, loss, (float *)ctx->ws,
+                                           (cudaStream_t)stream));
+}
+
+rt_status rt_mlp_adamw(rt_ctx *ctx, float *master, uint16_t *wb, const float *grad, float *m, float *v, int step,
+                       float lr, float beta1, float beta2, float eps, float weight_decay, void *stream)
+{
+    if (!ctx || !master || !wb || !grad || !m || !v || step < 1) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    ctx->launches += 1;
+    return cuda_status(
+        launch_mlp_adamw(master, wb, grad, m, v, step, lr, beta1, beta2, eps, weight_decay, (cudaStream_t)stream));
+}
+
+int rt_last_picks(const rt_ctx *ctx, int *variants, int cap)
+{
+    if (!ctx) return 0;
+    const int n = ctx->n_last_picks < cap ? ctx->n_last_picks : cap;
+    for (int i = 0; variants && i < n; ++i) variants[i] = ctx->last_picks[i];
+    return ctx->n_last_picks;
+}
+
+rt_status rt_set_picker(rt_ctx *ctx, const uint16_t *wb, const float *norm)
+{
+    if (!ctx || (!wb) != (!norm)) return RT_EINVAL;
+    ctx->picker_wb = wb;
+    ctx->picker_norm = norm;
+    return RT_OK;
+}
+
 void rt_seg_params_default(rt_seg_params *p)
 {
     if (!p) return;
@@ -494,6 +610,7 @@ void rt_seg_params_default(rt_seg_params *p)
     p->conn_fill = 4;
     p->variant = RT_AUTO;
     p->max_local = 0;
+    p->policy = RT_POLICY_PLAIN;
 }
 
 rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_seg_params *params, void *stream)
@@ -504,6 +621,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
     if (P.conn_fill != 4 && P.conn_fill != 8) return RT_EINVAL;
     if (P.h_offset < 0 || P.h_offset > 255 || P.threshold < 0 || P.threshold > 256) return RT_EINVAL;
     if (P.variant < RT_AUTO || P.variant > RT_HYBRID) return RT_EINVAL;
+    if (P.policy != RT_POLICY_PLAIN && P.policy != RT_POLICY_LEARNED) return RT_EINVAL;
     int64_t maxN = 0;
     for (int i = 0; i < n; ++i) {
         const rt_tile &t = tiles[i];
@@ -532,9 +650,30 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
             maxH = b.img[i].H > maxH ? b.img[i].H : maxH;
             maxW = b.img[i].W > maxW ? b.img[i].W : maxW;
         }
+        const bool learned = P.policy == RT_POLICY_LEARNED && ctx->picker_wb && ctx->picker_norm;
+        FeatBatch fb;
+        float *feat = nullptr;
+        int32_t *picks_dev = nullptr;
         auto layout = [&](Carve &cv, ReconWs &w, std::vector<uint8_t *> &Bs, uint8_t *&Fw, char *&uf_ws,
                           char *&edt_ws) {
             carve_recon(cv, b, w);
+            if (learned) {
+                fb.n = cn;
+                for (int i = 0; i < cn; ++i) {
+                    const rt_tile &t = tiles[c0 + i];
+                    const size_t nb = (size_t)((t.H + 7) / 8) * ((t.W + 7) / 8);
+                    FeatImage &d = fb.img[i];
+                    d.img = t.img;
+                    d.ld = t.ld_img;
+                    d.H = t.H;
+                    d.W = t.W;
+                    d.hist = cv.take<uint32_t>(256);
+                    d.dark = cv.take<uint8_t>(nb);
+                    d.bmax = cv.take<uint8_t>(nb);
+                }
+                feat = cv.take<float>((size_t)cn * kNumFeatures);
+                picks_dev = cv.take<int32_t>((size_t)cn);
+            }
             Bs.resize(cn);
             for (int i = 0; i < cn; ++i) Bs[i] = cv.take<uint8_t>((size_t)b.img[i].H * b.img[i].W);
             Fw = cv.take<uint8_t>((size_t)maxN);
@@ -555,8 +694,44 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         layout(cv, w, Bs, Fw, uf_ws, edt_ws);
 
         RT_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
-        st = run_recon(ctx, b, w, P.conn_recon, P.variant, P.max_local, w.err, s);
-        if (st != RT_OK) return st;
+        if (!learned) {
+            st = run_recon(ctx, b, w, P.conn_recon, P.variant, P.max_local, w.err, s);
+            if (st != RT_OK) return st;
+        } else {
+            // the picker chooses a variant per tile; tiles are grouped by
+            // variant and each group propagates in its own launches
+            int picks[kMaxImgs];
+            {
+                Phase ph(ctx, RT_PHASE_PICK, s);
+                RT_CUDA_TRY(launch_features(fb, feat, s));
+                RT_CUDA_TRY(launch_mlp_forward(ctx->picker_wb, ctx->picker_norm, feat, cn, nullptr, nullptr,
+                                               picks_dev, s));
+                ctx->launches += 3;
+                RT_CUDA_TRY(cudaMemcpyAsync(picks, picks_dev, sizeof(int32_t) * cn, cudaMemcpyDeviceToHost, s));
+                RT_CUDA_TRY(cudaStreamSynchronize(s));
+            }
+            for (int i = 0; i < cn; ++i) {
+                const int v = picks[i] + 1;
+                ctx->last_picks[i] = (v >= RT_RASTER && v <= RT_HYBRID) ? v : (P.variant == RT_AUTO ? RT_RASTER : P.variant);
+            }
+            ctx->n_last_picks = cn;
+            for (int v = RT_RASTER; v <= RT_HYBRID; ++v) {
+                ReconBatch sb;
+                std::memset(&sb, 0, sizeof(sb));
+                for (int i = 0; i < cn; ++i) {
+                    if (ctx->last_picks[i] != v) continue;
+                    ReconImage d = b.img[i];
+                    d.tile_base = sb.ntiles;
+                    sb.ntiles += d.tiles_x * d.tiles_y;
+                    const int64_t words = (int64_t)d.Hp * d.Wp / 4;
+                    if (words > sb.max_words) sb.max_words = words;
+                    sb.img[sb.n++] = d;
+                }
+                if (sb.n == 0) continue;
+                st = run_recon(ctx, sb, w, P.conn_recon, v, P.max_local, w.err, s);
+                if (st != RT_OK) return st;
+            }
+        }
         for (int i = 0; i < cn; ++i) {
             const rt_tile &t = tiles[c0 + i];
             const ReconImage &d = b.img[i];

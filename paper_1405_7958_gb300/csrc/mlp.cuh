@@ -1,0 +1,29 @@
+// The learned variant picker's MLP (see mlp.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace rtk {
+
+constexpr int kMlpIn = 24, kMlpH = 64, kMlpOut = 3;
+// flat parameter vector: W1[64][24] b1[64] W2[64][64] b2[64] W3[3][64] b3[3]
+constexpr int kW1 = 0;
+constexpr int kB1 = kW1 + kMlpH * kMlpIn;
+constexpr int kW2 = kB1 + kMlpH;
+constexpr int kB2 = kW2 + kMlpH * kMlpH;
+constexpr int kW3 = kB2 + kMlpH;
+constexpr int kB3 = kW3 + kMlpOut * kMlpH;
+constexpr int kMlpParams = kB3 + kMlpOut;                 // 5955
+constexpr int kMlpAct = 2 * kMlpH;                        // saved h1, h2 per sample
+constexpr int kMlpDelta = kMlpOut + 2 * kMlpH + kMlpIn + 1;   // dz, dh2, dh1, xn, loss per sample
+
+cudaError_t launch_mlp_forward(const uint16_t *wb, const float *norm, const float *x, int B, float *logits, float *act,
+                               int32_t *pick, cudaStream_t s);
+size_t mlp_backward_workspace_bytes(int B);
+cudaError_t launch_mlp_backward(const uint16_t *wb, const float *norm, const float *x, const float *act,
+                                const float *logits, const int32_t *label, int B, float *grad, float *loss, float *ws,
+                                cudaStream_t s);
+cudaError_t launch_mlp_adamw(float *master, uint16_t *wb, const float *grad, float *m, float *v, int step, float lr,
+                             float b1, float b2, float eps, float wd, cudaStream_t s);
+
+}  // namespace rtk

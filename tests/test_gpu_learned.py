@@ -1,0 +1,143 @@
+"""GPU tests of the learned picker path and the GPU tile generator: the
+generator against the Python generator (bit-exact), the features and the
+network (forward, backward, AdamW) against the fp64 oracle, and the chain
+under the learned policy against the plain one (identical bytes)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import features as OF
+from oracle import mlp as OM
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import paper_1405_7958_gb300 as rt
+    return rt
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+GEN_CASES = [
+    dict(H=512, W=512, seed=1000, n_shapes=60, kind="disk", vlo=40, vhi=90, rmin=4, rmax=12, background="flat"),
+    dict(H=700, W=1031, seed=7, n_shapes=150, kind="ellipse"),
+    dict(H=1, W=300, seed=3, n_shapes=2, kind="ellipse"),
+    dict(H=600, W=520, seed=2**40 + 5, n_shapes=0, kind="ellipse"),
+    dict(H=300, W=300, seed=11, n_shapes=40, kind="ellipse", noise=False),
+]
+
+
+@pytest.mark.parametrize("case", GEN_CASES)
+def test_gpu_generator_matches_python(rt, case):
+    want = synth.tile(**case)
+    got = host(rt.synth_tile(**case))
+    assert np.array_equal(got, want)
+
+
+def test_gpu_generator_4k_tile(rt):
+    assert np.array_equal(host(rt.config2_tile(2003)), synth.config2_tile(2003))
+
+
+def test_features_match_oracle(rt):
+    imgs = [synth.config2_tile(5, H=333, W=517), synth.config1_image(1000), synth.random_binary(64, 40, 2, 500) * 200,
+            np.full((9, 13), 77, np.uint8), synth.config2_tile(9, H=1024, W=2048)]
+    got = host(rt.tile_features([torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in imgs]))
+    for g, x in zip(got, imgs):
+        want = OF.features(x)
+        assert np.array_equal(g[7:16], want[7:16])                       # percentiles are integers
+        assert np.allclose(g, want, rtol=2e-6, atol=2e-6), (g - want)
+
+
+def _picker_inputs(rng, B):
+    x = rng.normal(size=(B, 24)).astype(np.float32) * 3 + 1
+    y = rng.integers(0, 3, size=B).astype(np.int32)
+    return x, y
+
+
+def test_mlp_forward_and_backward_match_oracle(rt):
+    rng = np.random.default_rng(0)
+    pk = rt.Picker(seed=1)
+    norm = np.concatenate([rng.normal(size=24), rng.uniform(0.5, 2.0, size=24)]).astype(np.float32)
+    pk.norm = torch.from_numpy(norm).cuda()
+    x, y = _picker_inputs(rng, 777)
+    xd = torch.from_numpy(x).cuda()
+    logits, act, pick = pk.forward(xd, with_act=True)
+    grad, loss = pk.backward(xd, act, logits, torch.from_numpy(y).cuda())
+    p = OM.bf16_bits_to_f64(host(pk.wb))
+    _, h1, h2, z = OM.forward(p, norm, x)
+    assert np.allclose(host(logits), z, rtol=1e-4, atol=1e-4)
+    assert np.array_equal(host(pick), z.argmax(axis=1))
+    assert np.allclose(host(act)[:, :64], h1, rtol=1e-4, atol=1e-4)
+    g_want = OM.backward(p, norm, x, y)
+    g_got = host(grad).astype(np.float64)
+    for name, shape in OM.SHAPES:
+        a, b = OM.unflatten(g_got)[name].ravel(), OM.unflatten(g_want)[name].ravel()
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-7, name
+        if np.linalg.norm(b) > 0:
+            assert a @ b / (np.linalg.norm(a) * np.linalg.norm(b)) > 0.999, name
+    assert np.isclose(float(host(loss)[0]), OM.loss(p, norm, x, y), rtol=1e-5)
+
+
+def test_adamw_step_matches_oracle(rt):
+    rng = np.random.default_rng(2)
+    pk = rt.Picker(seed=3)
+    g = rng.normal(size=pk.NPARAM).astype(np.float32)
+    pk.grad.copy_(torch.from_numpy(g))
+    master0 = host(pk.master).astype(np.float64)
+    pk.step(lr=1e-2, weight_decay=1e-3)
+    pk.step(lr=1e-2, weight_decay=1e-3)
+    m1, mm, vv = OM.adamw(master0, g.astype(np.float64), 0.0, 0.0, 1, 1e-2, wd=1e-3)
+    m2, _, _ = OM.adamw(m1, g.astype(np.float64), mm, vv, 2, 1e-2, wd=1e-3)
+    got = host(pk.master)
+    assert np.allclose(got, m2, rtol=1e-5, atol=1e-6)
+    # the bf16 copy is the master rounded to nearest even
+    want_bits = torch.from_numpy(got).to(torch.bfloat16).view(torch.int16).numpy()
+    assert np.array_equal(host(pk.wb), want_bits)
+
+
+def test_training_reduces_loss(rt):
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(512, 24)).astype(np.float32)
+    y = (x[:, 0] > 0.3).astype(np.int32) + (x[:, 1] > 0.8).astype(np.int32)
+    pk = rt.Picker(seed=5)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    pk.set_norm(xd)
+    losses = []
+    for _ in range(150):
+        logits, act, _ = pk.forward(xd, with_act=True)
+        _, loss = pk.backward(xd, act, logits, yd)
+        losses.append(float(loss.item()))
+        pk.step(lr=1e-2)
+    assert losses[-1] < 0.5 * losses[0]
+    _, _, pick = pk.forward(xd)
+    assert (host(pick) == y).mean() > 0.9
+
+
+def test_learned_policy_same_bytes_as_plain(rt):
+    imgs = [synth.config2_tile(40 + i, H=H, W=W) for i, (H, W) in enumerate([(300, 500), (640, 256), (1024, 1024)])]
+    d = [torch.from_numpy(x).cuda() for x in imgs]
+    pk = rt.Picker(seed=9)
+    # steer the untrained network to every class: bias b3 one-hot per run
+    for cls in range(3):
+        b3 = torch.full((3,), -10.0)
+        b3[cls] = 10.0
+        pk.master[5760:5952] = 0.0                 # W3 = 0: the logits are b3
+        pk.master[5952:5955] = b3.cuda()
+        pk.wb = pk.master.to(torch.bfloat16).view(torch.int16).contiguous()
+        ctx = rt.Context()
+        pk.attach(ctx)
+        outs = rt.segment_batch(d, rt.SegParams(policy=1), ctx=ctx)
+        assert rt.last_picks(ctx) == [cls + 1] * 3
+        for o, x in zip(outs, imgs):
+            want = oracle.chain(x)
+            for k in ("R", "F", "L", "D"):
+                assert np.array_equal(host(o[k]), want[k])
+        ctx.close()
