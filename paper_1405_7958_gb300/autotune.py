@@ -1,0 +1,70 @@
+"""Autotuner for the batched segmentation chain.
+
+The run-time knobs of the reconstruction are the propagation variant and the
+budget of sweep iterations per dense tile visit (`max_local`): a small
+budget revisits tiles more often, a large one sweeps tiles longer before
+their neighbours' news arrives. The tuner times each candidate on the batch
+itself (CUDA events on the launch stream, median of `reps`), keeps the
+fastest, and caches the choice per size class in a JSON table.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import torch
+
+import paper_1405_7958_gb300 as rt
+
+CANDIDATES = tuple((v, m) for v in (rt.RT_RASTER,) for m in (2, 4, 8, 16)) + ((rt.RT_HYBRID, 0),)
+
+
+def size_class(images) -> str:
+    """Bucket of a batch: number of tiles and total megapixels (rounded)."""
+    px = sum(int(x.shape[0]) * int(x.shape[1]) for x in images)
+    return f"n{len(images)}_mp{int(round(px / 2 ** 20))}"
+
+
+def tune(images, reps: int = 3, candidates=CANDIDATES, ctx=None, stream=None) -> dict:
+    ctx = ctx or rt.default_context(images[0].device.index)
+    stream = stream or torch.cuda.current_stream()
+    outs = None
+    best = None
+    results = []
+    for v, m in candidates:
+        p = rt.SegParams(variant=v, max_local=m)
+        outs = rt.segment_batch(images, p, outputs=outs, ctx=ctx, stream=stream)   # warm-up
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rt.segment_batch(images, p, outputs=outs, ctx=ctx, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        t = float(np.median(ts))
+        results.append({"variant": v, "max_local": m, "ms": t})
+        if best is None or t < best["ms"]:
+            best = results[-1]
+    return {"best": best, "all": results}
+
+
+class Table:
+    """Size class -> tuned parameters, persisted as JSON."""
+
+    def __init__(self, path: str):
+        self.path = path
+        self.t = {}
+        if os.path.exists(path):
+            with open(path) as fh:
+                self.t = json.load(fh)
+
+    def params(self, images, **tune_kw) -> rt.SegParams:
+        key = size_class(images)
+        if key not in self.t:
+            self.t[key] = tune(images, **tune_kw)["best"]
+            with open(self.path, "w") as fh:
+                json.dump(self.t, fh, indent=1)
+        b = self.t[key]
+        return rt.SegParams(variant=int(b["variant"]), max_local=int(b["max_local"]))
