@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving leg at 800 tiles/s (0: skip)")
     return ap.parse_args()
 
 
@@ -196,7 +197,12 @@ def run_native(a, rank, world, local_rank):
         torch.cuda.synchronize()
 
     ctx = rt.Context(local_rank)
-    params = rt.SegParams()
+    # the metric's configuration: batched, with the trained variant picker
+    from paper_1405_7958_gb300 import picker as pkmod
+    picker = pkmod.load(os.path.join(ROOT, "paper_1405_7958_gb300", "data", "picker_config4.npz"), device=dev)
+    picker.attach(ctx)
+    params = rt.SegParams(policy=1)
+    plain = rt.SegParams()
     stream = torch.cuda.current_stream()
     imgs = [torch.from_numpy(t).to(dev) for t in tiles]
     sampler = ClockSampler(local_rank)
@@ -232,6 +238,45 @@ def run_native(a, rank, world, local_rank):
     total_ms = float(t.item())
     px = a.size * a.size
     value = world * a.batch * a.steps / (total_ms / 1000.0)
+    picks = rt.last_picks(ctx)
+
+    def timed(fn, steps):
+        ms = []
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sum(ms)
+
+    k2 = max(5, a.steps // 4)
+    outs_p = rt.segment_batch(imgs, plain, ctx=ctx)
+    timed(lambda: rt.segment_batch(imgs, plain, outputs=outs_p, ctx=ctx), 2)
+    batched_plain = a.batch * k2 / (timed(lambda: rt.segment_batch(imgs, plain, outputs=outs_p, ctx=ctx), k2) / 1000)
+    outs1 = [rt.segment_batch([im], plain, ctx=ctx)[0] for im in imgs]
+
+    def per_tile():
+        for im, o in zip(imgs, outs1):
+            rt.segment_batch([im], plain, outputs=[o], ctx=ctx)
+
+    timed(per_tile, 1)
+    per_tile_plain = a.batch * k2 / (timed(per_tile, k2) / 1000)
+    # batched and plain produce the same bytes
+    for o_l, o_p, o_1 in zip(outs, outs_p, outs1):
+        assert torch.equal(o_l["L"], o_p["L"]) and torch.equal(o_l["D"], o_1["D"])
+
+    serving = None
+    if a.serve_seconds > 0 and world == 1:
+        from paper_1405_7958_gb300 import serve
+        spool = serve.make_pool(32, 5000, ctx=ctx)
+        serve.run_batched(serve.arrivals(50.0, 0.3, len(spool), 9, spool), spool, policy=1, picker=picker)
+        reqs = serve.arrivals(800.0, a.serve_seconds, len(spool), 801, spool)
+        serve.run_batched(reqs, spool, policy=1, picker=picker)
+        serving = {"rate_tiles_s": 800, "seconds": a.serve_seconds, "tiles": "512..4096 px sides",
+                   **serve.summarize(reqs, a.serve_seconds)}
 
     # dominant kernel: the propagation sweeps (one launch per step)
     sweep_ms, sweep_n = phases["recon_sweep"]
@@ -241,7 +286,7 @@ def run_native(a, rank, world, local_rank):
         per_launch_s = sweep_ms / sweep_n / 1000.0
         algo_bytes = BYTES_RECON * px * a.batch
         ach = algo_bytes / per_launch_s / 1e9
-        roof = {"kernel": "recon_sweep_kernel", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+        roof = {"kernel": "recon_persistent_kernel<8,0>", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
                 "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": per_launch_s * 1000}
 
@@ -303,6 +348,11 @@ def run_native(a, rank, world, local_rank):
             "roofline": roof,
             "phases_ms_per_step": {k: v[0] / a.steps for k, v in phases.items()},
             "recon_visits_iterations_per_step": visits,
+            "batched_learned_tiles_s": value,
+            "batched_plain_tiles_s": world * batched_plain,
+            "plain_per_tile_tiles_s": world * per_tile_plain,
+            "picker_choices": picks,
+            "serving_batched_learned": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
