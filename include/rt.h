@@ -285,7 +285,11 @@ RT_API rt_status rt_set_picker(rt_ctx *ctx, const uint16_t *wb, const float *nor
 
 /* Variants (RT_RASTER..RT_HYBRID) the picker chose for the tiles of the last
  * chunk (up to 32 tiles) of the last learned rt_segment_batch call; copies up
- * to cap of them into variants (nullable) and returns how many there were. */
+ * to cap of them into variants (nullable) and returns how many there were.
+ * The choices stay on the device during the call (the propagation reads
+ * them there) and are copied to pinned host memory at its end; this call
+ * waits for that copy. After the replay of a captured graph the caller
+ * synchronizes the stream first. Returns 0 on a CUDA error. */
 RT_API int rt_last_picks(const rt_ctx *ctx, int *variants, int cap);
 
 /* One tile of a batch. Every pointer is a device pointer. */

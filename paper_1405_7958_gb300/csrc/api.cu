@@ -31,7 +31,9 @@ struct rt_ctx {
     bool timing = false;
     const uint16_t *picker_wb = nullptr;   // attached picker (caller-owned device memory)
     const float *picker_norm = nullptr;
-    int last_picks[kMaxImgs] = {};          // variants the picker chose in the last chunk
+    int32_t *picks_host = nullptr;         // pinned: picker classes of the last learned chunk
+    cudaEvent_t picks_ev = nullptr;        // recorded after their copy (not under stream capture)
+    bool picks_ev_valid = false;
     int n_last_picks = 0;
     std::vector<PhaseRec> recs;
     std::vector<cudaEvent_t> pool;
@@ -147,16 +149,18 @@ rt_status cuda_status(cudaError_t e)
 // ---------------------------------------------------------------- recon
 struct ReconWs {
     uint32_t *flags;   // per tile
-    uint32_t *ctl;     // [0] pending, [1] visits, [2] dense iterations, [3] queue pops
+    uint32_t *ctl;     // kCtlWords control words (recon.cuh)
     int32_t *err;
+    int32_t *map;      // kGroups x ntiles tile lists when the variant is chosen per image
 };
 
 // Reserve the sweep control block and per-image padded buffers.
-void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w)
+void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w, bool grouped = false)
 {
     w.flags = cv.take<uint32_t>((size_t)b.ntiles);
-    w.ctl = cv.take<uint32_t>(8);
+    w.ctl = cv.take<uint32_t>(kCtlWords);
     w.err = cv.take<int32_t>(1);
+    w.map = grouped ? cv.take<int32_t>((size_t)kGroups * b.ntiles) : nullptr;
     for (int i = 0; i < b.n; ++i) {
         ReconImage &d = b.img[i];
         d.Rw = cv.take<uint8_t>((size_t)d.Hp * d.Wp);
@@ -165,39 +169,52 @@ void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w)
 }
 
 // Enqueue init + propagation for a batch whose buffers are carved. `err`
-// receives the device status.
+// receives the device status. With `pick` (device, one picker class per
+// image) every image propagates with its own variant: one launch per variant
+// group over the group's tile list, with no host round trip.
 rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int variant, int max_local, int32_t *err,
-                    cudaStream_t s)
+                    cudaStream_t s, const int32_t *pick = nullptr)
 {
     if (variant == RT_AUTO) variant = RT_RASTER;
     // RT_RASTER / RT_QUEUE: every tile starts flagged for a dense visit (the
     // queue visit then seeds every pixel); RT_HYBRID: nothing flagged, the
     // dense pass over all tiles flags what remains.
     const uint32_t flag0 = variant == RT_HYBRID ? 0u : 2u;
-    RT_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, 8 * sizeof(uint32_t), s));
+    RT_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, kCtlWords * sizeof(uint32_t), s));
     {
         Phase ph(ctx, RT_PHASE_RECON_INIT, s);
-        RT_CUDA_TRY(launch_recon_init(b, w.flags, w.ctl, flag0, err, s));
+        RT_CUDA_TRY(launch_recon_init(b, w.flags, w.ctl, flag0, pick, w.map, err, s));
         ctx->launches += 1;
     }
-    ctx->visits_dev = w.ctl + 1;
+    ctx->visits_dev = w.ctl + kCtlVisits;
     SweepParams p;
     p.b = b;
     p.ntiles = b.ntiles;
     p.flags = w.flags;
-    p.pending = w.ctl;
+    p.pending = w.ctl + kCtlPending;
     p.err = err;
-    p.visits = w.ctl + 1;
-    p.max_local = max_local > 0 ? max_local : (variant == RT_HYBRID ? 64 : 8);
+    p.visits = w.ctl + kCtlVisits;
     p.timeout_ns = kSweepTimeoutNs;
+    p.map = nullptr;
+    p.nvirt = nullptr;
     int grid = 0;
     Phase ph(ctx, RT_PHASE_RECON_SWEEP, s);
-    if (variant == RT_HYBRID) {
-        RT_CUDA_TRY(launch_recon_dense(p, conn, s));
+    for (int g = 0; g < (pick ? kGroups : 1); ++g) {
+        const int v = pick ? RT_RASTER + g : variant;
+        if (pick) {
+            p.map = w.map + (size_t)g * b.ntiles;
+            p.nvirt = w.ctl + kCtlGroupCount + g;
+            p.pending = w.ctl + kCtlGroupPending + g;
+        }
+        p.max_local = max_local > 0 ? max_local : (v == RT_HYBRID ? 64 : 8);
+        if (v == RT_HYBRID) {
+            RT_CUDA_TRY(launch_recon_dense(p, conn, s));
+            ctx->launches += 1;
+        }
         ctx->launches += 1;
+        RT_CUDA_TRY(launch_recon_persistent(p, conn, v == RT_RASTER ? 0 : 1, ctx->num_sms, s, &grid));
     }
-    ctx->launches += 1;
-    return cuda_status(launch_recon_persistent(p, conn, variant == RT_RASTER ? 0 : 1, ctx->num_sms, s, &grid));
+    return RT_OK;
 }
 
 void add_image(ReconBatch &b, const uint8_t *marker, int64_t ld_marker, const uint8_t *mask, int64_t ld_mask,
@@ -270,8 +287,12 @@ rt_status rt_create(rt_ctx **ctx, int device)
     rt_ctx *c = new (std::nothrow) rt_ctx;
     if (!c) return RT_ENOMEM;
     c->device = device;
-    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    DeviceGuard g(device);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->picks_host, kMaxImgs * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->picks_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (c->picks_host) cudaFreeHost(c->picks_host);
         delete c;
         return RT_ECUDA;
     }
@@ -292,6 +313,8 @@ void rt_destroy(rt_ctx *ctx)
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->picks_ev) cudaEventDestroy(ctx->picks_ev);
+    if (ctx->picks_host) cudaFreeHost(ctx->picks_host);
     delete ctx;
 }
 
@@ -536,6 +559,7 @@ rt_status rt_tile_features(rt_ctx *ctx, const uint8_t *const *imgs, const int64_
             d.H = Hs[i];
             d.W = Ws[i];
             d.hist = cv.take<uint32_t>(256);
+            d.acc = cv.take<unsigned long long>(4);
             d.dark = cv.take<uint8_t>(nb);
             d.bmax = cv.take<uint8_t>(nb);
         }
@@ -548,7 +572,7 @@ rt_status rt_tile_features(rt_ctx *ctx, const uint8_t *const *imgs, const int64_
     cv = Carve();
     cv.base = (char *)ctx->ws;
     layout(cv, fb);
-    ctx->launches += 2;
+    ctx->launches += 3;
     return cuda_status(launch_features(fb, out, s));
 }
 
@@ -586,8 +610,18 @@ rt_status rt_mlp_adamw(rt_ctx *ctx, float *master, uint16_t *wb, const float *gr
 int rt_last_picks(const rt_ctx *ctx, int *variants, int cap)
 {
     if (!ctx) return 0;
+    if (ctx->picks_ev_valid) {
+        DeviceGuard g(ctx->device);
+        if (cudaEventSynchronize(ctx->picks_ev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+    }
     const int n = ctx->n_last_picks < cap ? ctx->n_last_picks : cap;
-    for (int i = 0; variants && i < n; ++i) variants[i] = ctx->last_picks[i];
+    for (int i = 0; variants && i < n; ++i) {
+        const int g = ctx->picks_host[i];
+        variants[i] = (g >= 0 && g < kGroups) ? RT_RASTER + g : RT_RASTER;
+    }
     return ctx->n_last_picks;
 }
 
@@ -656,7 +690,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         int32_t *picks_dev = nullptr;
         auto layout = [&](Carve &cv, ReconWs &w, std::vector<uint8_t *> &Bs, uint8_t *&Fw, char *&uf_ws,
                           char *&edt_ws) {
-            carve_recon(cv, b, w);
+            carve_recon(cv, b, w, learned);
             if (learned) {
                 fb.n = cn;
                 for (int i = 0; i < cn; ++i) {
@@ -668,6 +702,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
                     d.H = t.H;
                     d.W = t.W;
                     d.hist = cv.take<uint32_t>(256);
+                    d.acc = cv.take<unsigned long long>(4);
                     d.dark = cv.take<uint8_t>(nb);
                     d.bmax = cv.take<uint8_t>(nb);
                 }
@@ -698,39 +733,23 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
             st = run_recon(ctx, b, w, P.conn_recon, P.variant, P.max_local, w.err, s);
             if (st != RT_OK) return st;
         } else {
-            // the picker chooses a variant per tile; tiles are grouped by
-            // variant and each group propagates in its own launches
-            int picks[kMaxImgs];
+            // the picker chooses a variant per tile on the device; the
+            // propagation reads its choices directly (no host round trip)
             {
                 Phase ph(ctx, RT_PHASE_PICK, s);
                 RT_CUDA_TRY(launch_features(fb, feat, s));
                 RT_CUDA_TRY(launch_mlp_forward(ctx->picker_wb, ctx->picker_norm, feat, cn, nullptr, nullptr,
                                                picks_dev, s));
-                ctx->launches += 3;
-                RT_CUDA_TRY(cudaMemcpyAsync(picks, picks_dev, sizeof(int32_t) * cn, cudaMemcpyDeviceToHost, s));
-                RT_CUDA_TRY(cudaStreamSynchronize(s));
+                ctx->launches += 4;
             }
-            for (int i = 0; i < cn; ++i) {
-                const int v = picks[i] + 1;
-                ctx->last_picks[i] = (v >= RT_RASTER && v <= RT_HYBRID) ? v : (P.variant == RT_AUTO ? RT_RASTER : P.variant);
-            }
+            st = run_recon(ctx, b, w, P.conn_recon, P.variant, P.max_local, w.err, s, picks_dev);
+            if (st != RT_OK) return st;
+            RT_CUDA_TRY(cudaMemcpyAsync(ctx->picks_host, picks_dev, sizeof(int32_t) * cn, cudaMemcpyDeviceToHost, s));
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusActive;
+            if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cudaGetLastError();
+            ctx->picks_ev_valid = cap == cudaStreamCaptureStatusNone;
+            if (ctx->picks_ev_valid) RT_CUDA_TRY(cudaEventRecord(ctx->picks_ev, s));
             ctx->n_last_picks = cn;
-            for (int v = RT_RASTER; v <= RT_HYBRID; ++v) {
-                ReconBatch sb;
-                std::memset(&sb, 0, sizeof(sb));
-                for (int i = 0; i < cn; ++i) {
-                    if (ctx->last_picks[i] != v) continue;
-                    ReconImage d = b.img[i];
-                    d.tile_base = sb.ntiles;
-                    sb.ntiles += d.tiles_x * d.tiles_y;
-                    const int64_t words = (int64_t)d.Hp * d.Wp / 4;
-                    if (words > sb.max_words) sb.max_words = words;
-                    sb.img[sb.n++] = d;
-                }
-                if (sb.n == 0) continue;
-                st = run_recon(ctx, sb, w, P.conn_recon, v, P.max_local, w.err, s);
-                if (st != RT_OK) return st;
-            }
         }
         for (int i = 0; i < cn; ++i) {
             const rt_tile &t = tiles[c0 + i];

@@ -18,41 +18,93 @@
 
 namespace rtk {
 
-// one thread per 8 x 8 block: histogram (shared, then global), dark count,
-// block maximum
-__global__ void feat_block_kernel(FeatBatch fb)
+// pass 1, CTA = 64 rows x 256 columns, thread = column: histogram (shared,
+// then global), and per 8 x 8 block the dark count and the maximum (reduced
+// over the 8 lanes of a block column)
+__global__ void __launch_bounds__(256) feat_block_kernel(FeatBatch fb)
 {
     __shared__ uint32_t sh[256];
-    const FeatImage &d = fb.img[blockIdx.y];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
+    const FeatImage &d = fb.img[blockIdx.z];
+    sh[threadIdx.x] = 0;
     __syncthreads();
-    const int bh = (d.H + 7) / 8, bw = (d.W + 7) / 8;
-    const int nb = bh * bw;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        const int br = b / bw, bc = b % bw;
-        const int r1 = min(d.H, br * 8 + 8), c1 = min(d.W, bc * 8 + 8);
-        int dark = 0, mx = 0;
-        for (int r = br * 8; r < r1; ++r) {
-            const uint8_t *row = d.img + (int64_t)r * d.ld;
-            for (int c = bc * 8; c < c1; ++c) {
-                const int v = row[c];
-                atomicAdd(sh + v, 1u);
-                dark += v < 80;
-                mx = max(mx, v);
+    const int c = blockIdx.x * 256 + threadIdx.x;
+    const int r0 = blockIdx.y * 64;
+    if (r0 < d.H && blockIdx.x * 256 < d.W) {
+        const int bw = (d.W + 7) / 8;
+        for (int g = 0; g < 8; ++g) {
+            const int rb = r0 + 8 * g;
+            if (rb >= d.H) break;
+            int dark = 0, mx = 0;
+            if (c < d.W) {
+                const int re = min(d.H, rb + 8);
+                for (int r = rb; r < re; ++r) {
+                    const int v = d.img[(int64_t)r * d.ld + c];
+                    atomicAdd(sh + v, 1u);
+                    dark += v < 80;
+                    mx = max(mx, v);
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                dark += __shfl_xor_sync(0xffffffffu, dark, o);
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if ((threadIdx.x & 7) == 0 && c < d.W) {
+                const int b = (rb / 8) * bw + c / 8;
+                d.dark[b] = (uint8_t)dark;
+                d.bmax[b] = (uint8_t)mx;
             }
         }
-        d.dark[b] = (uint8_t)dark;
-        d.bmax[b] = (uint8_t)mx;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
-        if (sh[i]) atomicAdd(d.hist + i, sh[i]);
+    if (sh[threadIdx.x]) atomicAdd(d.hist + threadIdx.x, sh[threadIdx.x]);
 }
 
 __device__ __forceinline__ int marker_of(const uint8_t *D, int bh, int bw, int r, int c)
 {
     const int v = D[r * bw + c];
     return (r == 0 || c == 0 || r == bh - 1 || c == bw - 1) ? v : max(v - 30, 0);
+}
+
+// pass 2, thread per 8 x 8 block: integer sums over the full blocks (dark
+// count, its square, blocks above 10 %) and the frontier count
+__global__ void feat_count_kernel(FeatBatch fb)
+{
+    const FeatImage &d = fb.img[blockIdx.y];
+    const int bh = (d.H + 7) / 8, bw = (d.W + 7) / 8;
+    const int fbh = d.H / 8, fbw = d.W / 8;       // full blocks
+    const int nb = bh * bw;
+    unsigned long long s1 = 0, s2 = 0, over = 0, front = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const int br = b / bw, bc = b % bw;
+        if (br < fbh && bc < fbw) {
+            const int k = d.dark[b];
+            s1 += k;
+            s2 += k * k;
+            over += 10 * k > 64;
+        }
+        const int Dp = d.bmax[b], Jp = marker_of(d.bmax, bh, bw, br, bc);
+        int best = -1;
+        if (br > 0) {
+            if (bc > 0) best = max(best, min(marker_of(d.bmax, bh, bw, br - 1, bc - 1), Dp));
+            best = max(best, min(marker_of(d.bmax, bh, bw, br - 1, bc), Dp));
+            if (bc + 1 < bw) best = max(best, min(marker_of(d.bmax, bh, bw, br - 1, bc + 1), Dp));
+        }
+        if (bc > 0) best = max(best, min(marker_of(d.bmax, bh, bw, br, bc - 1), Dp));
+        front += best > Jp;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        over += __shfl_down_sync(0xffffffffu, over, o);
+        front += __shfl_down_sync(0xffffffffu, front, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(d.acc + 0, s1);
+        atomicAdd(d.acc + 1, s2);
+        atomicAdd(d.acc + 2, over);
+        atomicAdd(d.acc + 3, front);
+    }
 }
 
 template <typename T>
@@ -69,105 +121,109 @@ __device__ __forceinline__ T block_sum(T v, T *red)
     return s;   // valid in thread 0
 }
 
-// one CTA per image: block statistics, frontier count, histogram statistics
-__global__ void __launch_bounds__(1024) feat_final_kernel(FeatBatch fb, float *out)
+// pass 3, CTA of 256 threads per image (thread = histogram bin): moments,
+// entropy and percentiles from the histogram; the partial edge blocks; the
+// 24 features
+__global__ void __launch_bounds__(256) feat_final_kernel(FeatBatch fb, float *out)
 {
-    __shared__ double redd[32];
-    __shared__ long long redl[32];
+    __shared__ double redd[8];
+    __shared__ uint32_t cum[256];
     const FeatImage &d = fb.img[blockIdx.x];
-    const int bh = (d.H + 7) / 8, bw = (d.W + 7) / 8;
-    const int nb = bh * bw;
-    double s1 = 0.0, s2 = 0.0;
-    long long over = 0, front = 0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int br = b / bw, bc = b % bw;
-        const int npx = (min(d.H, br * 8 + 8) - br * 8) * (min(d.W, bc * 8 + 8) - bc * 8);
-        const double fr = (double)d.dark[b] / npx;
-        s1 += fr;
-        s2 += fr * fr;
-        over += fr > 0.1;
-        const int Dp = d.bmax[b], Jp = marker_of(d.bmax, bh, bw, br, bc);
-        int best = -1;
-        if (br > 0) {
-            if (bc > 0) best = max(best, min(marker_of(d.bmax, bh, bw, br - 1, bc - 1), Dp));
-            best = max(best, min(marker_of(d.bmax, bh, bw, br - 1, bc), Dp));
-            if (bc + 1 < bw) best = max(best, min(marker_of(d.bmax, bh, bw, br - 1, bc + 1), Dp));
-        }
-        if (bc > 0) best = max(best, min(marker_of(d.bmax, bh, bw, br, bc - 1), Dp));
-        front += best > Jp;
-    }
-    s1 = block_sum(s1, redd);
-    s2 = block_sum(s2, redd);
-    over = block_sum(over, redl);
-    front = block_sum(front, redl);
-    if (threadIdx.x != 0) return;
-    float *f = out + (int64_t)blockIdx.x * kNumFeatures;
+    const int v = threadIdx.x;
     const double N = (double)d.H * d.W;
+    const uint32_t h = d.hist[v];
+    const double p = h / N;
+    const double mean_all = block_sum(p * v, redd);
+    __shared__ double s_mean;
+    if (v == 0) s_mean = mean_all;
+    __syncthreads();
+    const double mean = s_mean, x = v - mean;
+    const double m2 = block_sum(p * x * x, redd);
+    const double m3 = block_sum(p * x * x * x, redd);
+    const double m4 = block_sum(p * x * x * x * x, redd);
+    const double ent = block_sum(p > 0 ? -p * log2(p) : 0.0, redd);
+    // inclusive prefix sum of the histogram (Hillis-Steele in shared memory)
+    cum[v] = h;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        const uint32_t add = v >= o ? cum[v - o] : 0u;
+        __syncthreads();
+        cum[v] += add;
+        __syncthreads();
+    }
+    float *f = out + (int64_t)blockIdx.x * kNumFeatures;
+    const int pct[9] = {1, 5, 10, 25, 50, 75, 90, 95, 99};
+    for (int k = 0; k < 9; ++k) {
+        const double need = pct[k] / 100.0 * N;
+        if ((double)cum[v] >= need && (v == 0 || (double)cum[v - 1] < need)) f[7 + k] = (float)v;
+    }
+    // partial blocks on the right column and the bottom row
+    const int bh = (d.H + 7) / 8, bw = (d.W + 7) / 8;
+    const int fbh = d.H / 8, fbw = d.W / 8;
+    double ps1 = 0.0, ps2 = 0.0, pov = 0.0;
+    const int npart = (bw > fbw ? bh : 0) + (bh > fbh ? fbw : 0);
+    for (int i = v; i < npart; i += blockDim.x) {
+        int br, bc;
+        if (bw > fbw && i < bh) { br = i; bc = bw - 1; }
+        else { br = bh - 1; bc = i - (bw > fbw ? bh : 0); }
+        const int npx = (min(d.H, br * 8 + 8) - br * 8) * (min(d.W, bc * 8 + 8) - bc * 8);
+        const int k = d.dark[br * bw + bc];
+        const double fr = (double)k / npx;
+        ps1 += fr;
+        ps2 += fr * fr;
+        pov += 10 * k > npx;
+    }
+    ps1 = block_sum(ps1, redd);
+    ps2 = block_sum(ps2, redd);
+    pov = block_sum(pov, redd);
+    if (v != 0) return;
+    const double nb = (double)bh * bw;
     f[0] = (float)d.H;
     f[1] = (float)d.W;
     f[2] = (float)log(N);
-    double mean = 0.0;
-    for (int v = 0; v < 256; ++v) mean += (d.hist[v] / N) * v;
-    double m2 = 0.0, m3 = 0.0, m4 = 0.0, ent = 0.0;
-    for (int v = 0; v < 256; ++v) {
-        const double p = d.hist[v] / N, x = v - mean;
-        m2 += p * x * x;
-        m3 += p * x * x * x;
-        m4 += p * x * x * x * x;
-        if (p > 0) ent -= p * log2(p);
-    }
     f[3] = (float)mean;
     f[4] = (float)m2;
     f[5] = m2 > 0 ? (float)(m3 / (m2 * sqrt(m2))) : 0.f;
     f[6] = m2 > 0 ? (float)(m4 / (m2 * m2)) : 0.f;
-    const int pct[9] = {1, 5, 10, 25, 50, 75, 90, 95, 99};
-    for (int k = 0; k < 9; ++k) {
-        const double need = pct[k] / 100.0 * N;
-        uint64_t cum = 0;
-        int v = 0;
-        for (; v < 256; ++v) {
-            cum += d.hist[v];
-            if ((double)cum >= need) break;
-        }
-        f[7 + k] = (float)v;
-    }
-    uint64_t lo80 = 0, lo110 = 0;
-    for (int v = 0; v < 110; ++v) {
-        if (v < 80) lo80 += d.hist[v];
-        lo110 += d.hist[v];
-    }
-    f[16] = (float)(lo80 / N);
-    f[17] = (float)(lo110 / N);
+    f[16] = (float)(cum[79] / N);
+    f[17] = (float)(cum[109] / N);
     f[18] = (float)ent;
+    const double s1 = d.acc[0] / 64.0 + ps1, s2 = d.acc[1] / 4096.0 + ps2;
     const double mfr = s1 / nb;
     f[19] = (float)mfr;
     f[20] = (float)sqrt(fmax(s2 / nb - mfr * mfr, 0.0));
-    f[21] = (float)((double)over / nb);
-    f[22] = (float)((double)front / nb);
-    f[23] = (float)log1p((double)front);
+    f[21] = (float)(((double)d.acc[2] + pov) / nb);
+    f[22] = (float)((double)d.acc[3] / nb);
+    f[23] = (float)log1p((double)d.acc[3]);
 }
 
 size_t feat_workspace_bytes(int H, int W)
 {
     const size_t nb = (size_t)((H + 7) / 8) * ((W + 7) / 8);
-    return 256 * sizeof(uint32_t) + 2 * nb + 3 * 256;
+    return 256 * sizeof(uint32_t) + 4 * sizeof(unsigned long long) + 2 * nb + 4 * 256;
 }
 
 cudaError_t launch_features(const FeatBatch &fb, float *out, cudaStream_t s)
 {
-    int maxnb = 1;
+    int maxH = 1, maxW = 1, maxnb = 1;
     for (int i = 0; i < fb.n; ++i) {
-        const int nb = ((fb.img[i].H + 7) / 8) * ((fb.img[i].W + 7) / 8);
+        const FeatImage &d = fb.img[i];
+        maxH = d.H > maxH ? d.H : maxH;
+        maxW = d.W > maxW ? d.W : maxW;
+        const int nb = ((d.H + 7) / 8) * ((d.W + 7) / 8);
         maxnb = nb > maxnb ? nb : maxnb;
-        cudaError_t e = cudaMemsetAsync(fb.img[i].hist, 0, 256 * sizeof(uint32_t), s);
+        cudaError_t e = cudaMemsetAsync(d.hist, 0, 256 * sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.acc, 0, 4 * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
-    int gx = (int)ceil_div(maxnb, 256);
-    if (gx > 1024) gx = 1024;
-    feat_block_kernel<<<dim3((unsigned)gx, (unsigned)fb.n), 256, 0, s>>>(fb);
+    feat_block_kernel<<<dim3((unsigned)ceil_div(maxW, 256), (unsigned)ceil_div(maxH, 64), (unsigned)fb.n), 256, 0, s>>>(fb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    feat_final_kernel<<<(unsigned)fb.n, 1024, 0, s>>>(fb, out);
+    int gx = (int)ceil_div(maxnb, 256);
+    if (gx > 512) gx = 512;
+    feat_count_kernel<<<dim3((unsigned)gx, (unsigned)fb.n), 256, 0, s>>>(fb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    feat_final_kernel<<<(unsigned)fb.n, 256, 0, s>>>(fb, out);
     return cudaGetLastError();
 }
 

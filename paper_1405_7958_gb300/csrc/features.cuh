@@ -15,6 +15,7 @@ struct FeatImage {
     uint32_t *hist;   // workspace: 256 bins
     uint8_t *dark;    // workspace: dark pixels per 8 x 8 block
     uint8_t *bmax;    // workspace: maximum per 8 x 8 block
+    unsigned long long *acc;   // workspace: full-block sums of dark, dark^2, blocks > 10 %, frontier count
 };
 
 struct FeatBatch {

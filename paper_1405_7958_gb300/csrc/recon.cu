@@ -35,14 +35,42 @@ constexpr int kWarpWords = 2 * kTH * kTS + 2 * (kTH + 2);
 
 // ---------------------------------------------------------------- init
 // Iw = mask (0 in the padding), Rw = min(J, I). One thread per 4 pixels.
-__global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t *pending, uint32_t flag0,
-                                  int32_t *err)
+__device__ __forceinline__ int pick_group(const int32_t *pick, int i)
 {
-    if (blockIdx.y == 0) {
-        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.ntiles; t += gridDim.x * blockDim.x) flags[t] = flag0;
-        if (blockIdx.x == 0 && threadIdx.x == 0) *pending = flag0 ? (uint32_t)b.ntiles : 0u;
+    const int g = pick[i];
+    return (g >= 0 && g < kGroups) ? g : 0;
+}
+
+__global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
+                                  const int32_t *pick, int32_t *map, int32_t *err)
+{
+    const int i = blockIdx.y;
+    const ReconImage &d = b.img[i];
+    const int nt = d.tiles_x * d.tiles_y;
+    if (!pick) {
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nt; k += gridDim.x * blockDim.x)
+            flags[d.tile_base + k] = flag0;
+        if (i == 0 && blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlPending] = flag0 ? (uint32_t)b.ntiles : 0u;
+    } else {
+        const int g = pick_group(pick, i);
+        int off = 0;   // tiles of group g in the images before this one
+        for (int j = 0; j < i; ++j)
+            if (pick_group(pick, j) == g) off += b.img[j].tiles_x * b.img[j].tiles_y;
+        int32_t *mg = map + (int64_t)g * b.ntiles + off;
+        const uint32_t f0 = g == 2 ? 0u : 2u;
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nt; k += gridDim.x * blockDim.x) {
+            flags[d.tile_base + k] = f0;
+            mg[k] = d.tile_base + k;
+        }
+        if (i == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+            uint32_t cnt[kGroups] = {0u, 0u, 0u};
+            for (int j = 0; j < b.n; ++j) cnt[pick_group(pick, j)] += b.img[j].tiles_x * b.img[j].tiles_y;
+            for (int q = 0; q < kGroups; ++q) {
+                ctl[kCtlGroupCount + q] = cnt[q];
+                ctl[kCtlGroupPending + q] = q == 2 ? 0u : cnt[q];
+            }
+        }
     }
-    const ReconImage &d = b.img[blockIdx.y];
     const int64_t wpr = d.Wp / 4;
     const int64_t nwords = (int64_t)d.Hp * wpr;
     bool bad = false;
@@ -76,14 +104,15 @@ __global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t 
     if (bad) raise_status(err, RT_EMARKER);
 }
 
-cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *pending, uint32_t flag0,
-                              int32_t *err, cudaStream_t s)
+cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
+                              const int32_t *pick, int32_t *map, int32_t *err, cudaStream_t s)
 {
+    if (pick && !map) return cudaErrorInvalidValue;
     const int threads = 256;
     int64_t blocks = ceil_div(b.max_words, threads);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    recon_init_kernel<<<dim3((unsigned)blocks, (unsigned)b.n), threads, 0, s>>>(b, flags, pending, flag0, err);
+    recon_init_kernel<<<dim3((unsigned)blocks, (unsigned)b.n), threads, 0, s>>>(b, flags, ctl, flag0, pick, map, err);
     return cudaGetLastError();
 }
 
@@ -491,8 +520,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_dense_kernel(SweepPar
 {
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * kWarpsPerCta + warp;
-    if (t >= p.ntiles) return;
+    const int v = blockIdx.x * kWarpsPerCta + warp;
+    const int n = p.nvirt ? (int)*p.nvirt : p.ntiles;
+    if (v >= n) return;
+    const int t = p.map ? p.map[v] : v;
     WarpBuf wb;
     wb.sRT = smem + warp * kWarpWords;
     wb.sIT = wb.sRT + kTH * kTS;
@@ -535,22 +566,24 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 5) recon_persis
     }
     const int gw = blockIdx.x * kWarpsPerCta + warp;
     const int nw = gridDim.x * kWarpsPerCta;
-    const int chunk = (p.ntiles + nw - 1) / nw;
+    const int n = p.nvirt ? (int)*p.nvirt : p.ntiles;
+    const int chunk = (n + nw - 1) / nw;
     const int own0 = gw * chunk;
-    const int own1 = min(p.ntiles, own0 + chunk);
+    const int own1 = min(n, own0 + chunk);
     const uint64_t t_start = globaltimer_ns();
     uint32_t nvisits = 0, work = 0;
     int idle = 0;
     for (;;) {
         bool did = false;
         for (int base = own0; base < own1; base += 32) {
-            const int tl = base + lane;
-            const bool f = tl < own1 && *reinterpret_cast<volatile uint32_t *>(p.flags + tl) != 0u;
+            const int vl = base + lane;
+            const int tl = vl < own1 ? (p.map ? p.map[vl] : vl) : 0;
+            const bool f = vl < own1 && *reinterpret_cast<volatile uint32_t *>(p.flags + tl) != 0u;
             uint32_t mask = __ballot_sync(0xffffffffu, f);
             while (mask) {
                 const int i = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const int t = base + i;
+                const int t = __shfl_sync(0xffffffffu, tl, i);
                 uint32_t got = 0;
                 if (lane == 0) got = atomicExch(p.flags + t, 0u);
                 got = __shfl_sync(0xffffffffu, got, 0);

@@ -45,13 +45,31 @@ struct SweepParams {
     uint32_t *visits;         // [0] tile visits, [1] dense iterations, [2] queue pops (statistics)
     int max_local;            // local iterations per visit before revisiting
     uint64_t timeout_ns;      // bound on the whole propagation
+    const int32_t *map;       // NULL: the launch covers tiles 0..ntiles-1; else its k-th tile is map[k]
+    const uint32_t *nvirt;    // with map: number of tiles the launch covers (device word)
 };
+
+// Control words of a propagation (device, zeroed before the init kernel):
+// kCtlPending: pending count of an ungrouped launch; kCtlVisits..+2: the
+// statistics; kCtlGroupPending + g / kCtlGroupCount + g: pending count and
+// number of tiles of variant group g when the variant is chosen per image.
+constexpr int kCtlPending = 0;
+constexpr int kCtlVisits = 1;
+constexpr int kCtlGroupPending = 4;
+constexpr int kCtlGroupCount = 8;
+constexpr int kCtlWords = 16;
+constexpr int kGroups = 3;    // RT_RASTER, RT_QUEUE, RT_HYBRID
 
 void plan_recon_image(ReconImage &d, int H, int W);
 cudaError_t launch_marker(const uint8_t *mask, int64_t ld_mask, uint8_t *marker, int64_t ld_marker, int H,
                           int W, int h_offset, cudaStream_t s);
-cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *pending, uint32_t flag0,
-                              int32_t *err, cudaStream_t s);
+// pick == NULL: every tile starts with flag0, ctl[kCtlPending] counts them.
+// pick != NULL (device, one entry per image, 0 raster / 1 queue / 2 hybrid,
+// anything else raster): tiles of raster and queue images start flagged,
+// hybrid ones not; map[g * ntiles + k] lists the tiles of group g in batch
+// order, with their count and pending count in ctl.
+cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
+                              const int32_t *pick, int32_t *map, int32_t *err, cudaStream_t s);
 // one dense visit of every tile (non-persistent)
 cudaError_t launch_recon_dense(const SweepParams &p, int conn, cudaStream_t s);
 // persistent visits of flagged tiles until quiescence; queue = 1: queue visits

@@ -141,3 +141,70 @@ def test_learned_policy_same_bytes_as_plain(rt):
             for k in ("R", "F", "L", "D"):
                 assert np.array_equal(host(o[k]), want[k])
         ctx.close()
+
+
+def _height_picker(rt):
+    """A hand-set network whose class depends on the tile height alone:
+    h = H / 1024, logits (0.5, h, 2h - 0.75) -> raster below H = 512, queue
+    below 768, hybrid above (all weights exact in bf16)."""
+    pk = rt.Picker(seed=0)
+    w = torch.zeros(pk.NPARAM, dtype=torch.float32)
+    w[0] = 2.0 ** -10                # W1[0][0]
+    w[1600] = 1.0                    # W2[0][0]
+    w[5760 + 64] = 1.0               # W3[1][0]
+    w[5760 + 128] = 2.0              # W3[2][0]
+    w[5952:5955] = torch.tensor([0.5, 0.0, -0.75])
+    pk.master.copy_(w)
+    pk.wb = pk.master.to(torch.bfloat16).view(torch.int16).contiguous()
+    pk.norm = torch.cat([torch.zeros(24), torch.ones(24)]).cuda()
+    return pk
+
+
+def test_learned_policy_mixed_variants_in_one_batch(rt):
+    """Tiles of one call take different variants (chosen on the device);
+    every tile still gives the oracle's bytes."""
+    shapes = [(1024, 700), (300, 500), (640, 256), (300, 300), (1100, 640), (700, 900)]
+    imgs = [synth.config2_tile(60 + i, H=H, W=W) for i, (H, W) in enumerate(shapes)]
+    d = [torch.from_numpy(x).cuda() for x in imgs]
+    pk = _height_picker(rt)
+    ctx = rt.Context()
+    pk.attach(ctx)
+    outs = rt.segment_batch(d, rt.SegParams(policy=1), ctx=ctx)
+    want_picks = [rt.RT_RASTER if H < 512 else rt.RT_QUEUE if H < 768 else rt.RT_HYBRID for H, _ in shapes]
+    assert rt.last_picks(ctx) == want_picks
+    for o, x in zip(outs, imgs):
+        want = oracle.chain(x)
+        for k in ("R", "F", "L", "D"):
+            assert np.array_equal(host(o[k]), want[k])
+    ctx.close()
+
+
+def test_learned_policy_in_cuda_graph(rt):
+    """The learned path has no host round trip, so it captures into a CUDA
+    graph; replays give the oracle's bytes and the same picks."""
+    shapes = [(300, 500), (700, 640), (1100, 333)]
+    imgs = [synth.config2_tile(80 + i, H=H, W=W) for i, (H, W) in enumerate(shapes)]
+    d = [torch.from_numpy(x).cuda() for x in imgs]
+    pk = _height_picker(rt)
+    ctx = rt.Context()
+    pk.attach(ctx)
+    s = torch.cuda.Stream()
+    p = rt.SegParams(policy=1)
+    with torch.cuda.stream(s):
+        outs = rt.segment_batch(d, p, ctx=ctx, stream=s)          # eager: allocates the workspace
+    s.synchronize()
+    for o in outs:
+        for k in ("R", "F", "L", "D"):
+            o[k].zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rt.segment_batch(d, p, outputs=outs, ctx=ctx, stream=s)
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert rt.last_picks(ctx) == [rt.RT_RASTER, rt.RT_QUEUE, rt.RT_HYBRID]
+        for o, x in zip(outs, imgs):
+            want = oracle.chain(x)
+            for k in ("R", "F", "L", "D"):
+                assert np.array_equal(host(o[k]), want[k])
+    ctx.close()
