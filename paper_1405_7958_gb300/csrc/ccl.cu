@@ -25,7 +25,8 @@
 namespace rtk {
 
 constexpr int kB = kUfBlock;
-constexpr int kRowsPerThread = 4;   // 256 threads: warp w owns rows 4w .. 4w+3
+constexpr int kRowsPerThread = 4;                     // warp w owns rows kRowsPerThread * w + 0, 1, ...
+constexpr int kThreads = 32 * kB / kRowsPerThread;    // threads per block CTA
 
 size_t uf_workspace_bytes(int H, int W)
 {
@@ -186,7 +187,7 @@ __device__ __forceinline__ int32_t global_index(const UfArgs &a, int local)
 
 // 1. block-local components, their roots, areas / border flags and edges
 template <int CONN>
-__global__ void __launch_bounds__(256) uf_local_kernel(UfArgs a, int source, bool count_area)
+__global__ void __launch_bounds__(kThreads) uf_local_kernel(UfArgs a, int source, bool count_area)
 {
     __shared__ int P[kB * kB];
     __shared__ int cnt[kB * kB];
@@ -299,8 +300,8 @@ cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, boo
     const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
     cudaError_t e = cudaMemsetAsync(a.nlist, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    if (conn == 8) uf_local_kernel<8><<<grid_blk, 256, 0, s>>>(a, source, count_area);
-    else uf_local_kernel<4><<<grid_blk, 256, 0, s>>>(a, source, count_area);
+    if (conn == 8) uf_local_kernel<8><<<grid_blk, kThreads, 0, s>>>(a, source, count_area);
+    else uf_local_kernel<4><<<grid_blk, kThreads, 0, s>>>(a, source, count_area);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (conn == 8) uf_border_kernel<8><<<grid_blk, 96, 0, s>>>(a);
     else uf_border_kernel<4><<<grid_blk, 96, 0, s>>>(a);
@@ -311,7 +312,7 @@ cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, boo
 
 // 4a. labels with the area filter
 template <int CONN>
-__global__ void __launch_bounds__(256) uf_labels_kernel(UfArgs a, int32_t *labels, int64_t ld_lab, int32_t amin,
+__global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfArgs a, int32_t *labels, int64_t ld_lab, int32_t amin,
                                                         int32_t amax, int32_t *n_kept)
 {
     __shared__ int P[kB * kB];
@@ -341,14 +342,14 @@ cudaError_t uf_labels_out(const UfArgs &a, int conn, int32_t *labels, int64_t ld
                           int32_t max_area, int32_t *n_kept, cudaStream_t s)
 {
     const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
-    if (conn == 8) uf_labels_kernel<8><<<grid_blk, 256, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
-    else uf_labels_kernel<4><<<grid_blk, 256, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
+    if (conn == 8) uf_labels_kernel<8><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
+    else uf_labels_kernel<4><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
     return cudaGetLastError();
 }
 
 // 4b. hole filling from the background components
 template <int CONN>
-__global__ void __launch_bounds__(256) uf_fill_kernel(UfArgs a, uint8_t *out, int64_t ld_out)
+__global__ void __launch_bounds__(kThreads) uf_fill_kernel(UfArgs a, uint8_t *out, int64_t ld_out)
 {
     __shared__ int P[kB * kB];
     __shared__ uint32_t M[kB];
@@ -369,8 +370,8 @@ __global__ void __launch_bounds__(256) uf_fill_kernel(UfArgs a, uint8_t *out, in
 cudaError_t uf_fill_out(const UfArgs &a, int conn, uint8_t *out, int64_t ld_out, cudaStream_t s)
 {
     const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
-    if (conn == 8) uf_fill_kernel<8><<<grid_blk, 256, 0, s>>>(a, out, ld_out);
-    else uf_fill_kernel<4><<<grid_blk, 256, 0, s>>>(a, out, ld_out);
+    if (conn == 8) uf_fill_kernel<8><<<grid_blk, kThreads, 0, s>>>(a, out, ld_out);
+    else uf_fill_kernel<4><<<grid_blk, kThreads, 0, s>>>(a, out, ld_out);
     return cudaGetLastError();
 }
 

@@ -41,78 +41,112 @@ __device__ __forceinline__ int pick_group(const int32_t *pick, int i)
     return (g >= 0 && g < kGroups) ? g : 0;
 }
 
+// Stores 16 bytes at p: one 16-byte store when p is 16-byte aligned, else bytes.
+__device__ __forceinline__ void store16(uint8_t *p, uint4 v, int n)
+{
+    if (n == 16 && ((uintptr_t)p & 15u) == 0) {
+        *reinterpret_cast<uint4 *>(p) = v;
+        return;
+    }
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    for (int k = 0; k < n; ++k) p[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+}
+
+// Loads n <= 16 bytes at p (zeros past n), with one 16-byte load when aligned.
+__device__ __forceinline__ uint4 load16(const uint8_t *p, int n)
+{
+    if (n == 16 && ((uintptr_t)p & 15u) == 0) return __ldg(reinterpret_cast<const uint4 *>(p));
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    for (int k = 0; k < n; ++k) w[k >> 2] |= (uint32_t)__ldg(p + k) << (8 * (k & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// One row of the batch per blockIdx.y, 16 padded columns per thread:
+// Iw = mask (0 in the padding), Rw = min(J, I); blocks of row 0 also set the
+// image's tile flags (and queue nothing: the propagation starts from them).
 __global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
                                   const int32_t *pick, int32_t *map, int32_t *err)
 {
-    const int i = blockIdx.y;
+    const int i = blockIdx.z;
     const ReconImage &d = b.img[i];
-    const int nt = d.tiles_x * d.tiles_y;
-    if (!pick) {
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nt; k += gridDim.x * blockDim.x)
-            flags[d.tile_base + k] = flag0;
-        if (i == 0 && blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlPending] = flag0 ? (uint32_t)b.ntiles : 0u;
-    } else {
-        const int g = pick_group(pick, i);
-        int off = 0;   // tiles of group g in the images before this one
-        for (int j = 0; j < i; ++j)
-            if (pick_group(pick, j) == g) off += b.img[j].tiles_x * b.img[j].tiles_y;
-        int32_t *mg = map + (int64_t)g * b.ntiles + off;
-        const uint32_t f0 = g == 2 ? 0u : 2u;
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nt; k += gridDim.x * blockDim.x) {
-            flags[d.tile_base + k] = f0;
-            mg[k] = d.tile_base + k;
-        }
-        if (i == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-            uint32_t cnt[kGroups] = {0u, 0u, 0u};
-            for (int j = 0; j < b.n; ++j) cnt[pick_group(pick, j)] += b.img[j].tiles_x * b.img[j].tiles_y;
-            for (int q = 0; q < kGroups; ++q) {
-                ctl[kCtlGroupCount + q] = cnt[q];
-                ctl[kCtlGroupPending + q] = q == 2 ? 0u : cnt[q];
+    if (blockIdx.y == 0) {
+        const int nt = d.tiles_x * d.tiles_y;
+        const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+        if (!pick) {
+            for (int k = tid; k < nt; k += nth) flags[d.tile_base + k] = flag0;
+            if (i == 0 && tid == 0) ctl[kCtlPending] = flag0 ? (uint32_t)b.ntiles : 0u;
+        } else {
+            const int g = pick_group(pick, i);
+            int off = 0;   // tiles of group g in the images before this one
+            for (int j = 0; j < i; ++j)
+                if (pick_group(pick, j) == g) off += b.img[j].tiles_x * b.img[j].tiles_y;
+            int32_t *mg = map + (int64_t)g * b.ntiles + off;
+            const uint32_t f0 = g == 2 ? 0u : 2u;
+            for (int k = tid; k < nt; k += nth) {
+                flags[d.tile_base + k] = f0;
+                mg[k] = d.tile_base + k;
             }
-        }
-    }
-    const int64_t wpr = d.Wp / 4;
-    const int64_t nwords = (int64_t)d.Hp * wpr;
-    bool bad = false;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
-         w += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(w / wpr);
-        const int c0 = (int)(w % wpr) * 4;
-        uint32_t iw = 0, rw = 0;
-        if (r < d.H) {
-            const bool border_row = (r == 0 || r == d.H - 1);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int c = c0 + b;
-                if (c < d.W) {
-                    const int iv = d.mask[(int64_t)r * d.ld_mask + c];
-                    int jv;
-                    if (d.marker) {
-                        jv = d.marker[(int64_t)r * d.ld_marker + c];
-                    } else {
-                        jv = (border_row || c == 0 || c == d.W - 1) ? iv : max(iv - d.h_offset, 0);
-                    }
-                    if (jv > iv) bad = true;
-                    iw |= (uint32_t)iv << (8 * b);
-                    rw |= (uint32_t)min(jv, iv) << (8 * b);
+            if (i == 0 && tid == 0) {
+                uint32_t cnt[kGroups] = {0u, 0u, 0u};
+                for (int j = 0; j < b.n; ++j) cnt[pick_group(pick, j)] += b.img[j].tiles_x * b.img[j].tiles_y;
+                for (int q = 0; q < kGroups; ++q) {
+                    ctl[kCtlGroupCount + q] = cnt[q];
+                    ctl[kCtlGroupPending + q] = q == 2 ? 0u : cnt[q];
                 }
             }
         }
-        reinterpret_cast<uint32_t *>(d.Iw)[w] = iw;
-        reinterpret_cast<uint32_t *>(d.Rw)[w] = rw;
     }
-    if (bad) raise_status(err, RT_EMARKER);
+    const int r = blockIdx.y;
+    const int c0 = (blockIdx.x * blockDim.x + threadIdx.x) * 16;
+    if (r >= d.Hp || c0 >= d.Wp) return;
+    uint4 iv = make_uint4(0u, 0u, 0u, 0u), rv = iv;
+    if (r < d.H && c0 < d.W) {
+        const int n = min(16, d.W - c0);
+        iv = load16(d.mask + (int64_t)r * d.ld_mask + c0, n);
+        uint32_t I[4] = {iv.x, iv.y, iv.z, iv.w}, J[4];
+        if (d.marker) {
+            const uint4 jv = load16(d.marker + (int64_t)r * d.ld_marker + c0, n);
+            J[0] = jv.x, J[1] = jv.y, J[2] = jv.z, J[3] = jv.w;
+        }
+        const bool border_row = r == 0 || r == d.H - 1;
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t rw = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = c0 + 4 * q + k;
+                const int ib = (I[q] >> (8 * k)) & 0xffu;
+                int jb;
+                if (d.marker) jb = (J[q] >> (8 * k)) & 0xffu;
+                else jb = (border_row || c == 0 || c == d.W - 1) ? ib : max(ib - d.h_offset, 0);
+                if (c < d.W) {
+                    bad |= jb > ib;
+                    rw |= (uint32_t)min(jb, ib) << (8 * k);
+                }
+            }
+            J[q] = rw;
+        }
+        rv = make_uint4(J[0], J[1], J[2], J[3]);
+        if (bad) raise_status(err, RT_EMARKER);
+    }
+    const int64_t o = (int64_t)r * d.Wp + c0;   // Wp is a multiple of 64 and the buffers 256-byte aligned
+    *reinterpret_cast<uint4 *>(d.Iw + o) = iv;
+    *reinterpret_cast<uint4 *>(d.Rw + o) = rv;
 }
 
 cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
                               const int32_t *pick, int32_t *map, int32_t *err, cudaStream_t s)
 {
     if (pick && !map) return cudaErrorInvalidValue;
-    const int threads = 256;
-    int64_t blocks = ceil_div(b.max_words, threads);
-    if (blocks > 4096) blocks = 4096;
-    if (blocks < 1) blocks = 1;
-    recon_init_kernel<<<dim3((unsigned)blocks, (unsigned)b.n), threads, 0, s>>>(b, flags, ctl, flag0, pick, map, err);
+    int maxHp = 1, maxWp = 16;
+    for (int i = 0; i < b.n; ++i) {
+        maxHp = b.img[i].Hp > maxHp ? b.img[i].Hp : maxHp;
+        maxWp = b.img[i].Wp > maxWp ? b.img[i].Wp : maxWp;
+    }
+    const int threads = 128;
+    const dim3 grid((unsigned)ceil_div(maxWp / 16, threads), (unsigned)maxHp, (unsigned)b.n);
+    recon_init_kernel<<<grid, threads, 0, s>>>(b, flags, ctl, flag0, pick, map, err);
     return cudaGetLastError();
 }
 
@@ -656,23 +690,37 @@ cudaError_t launch_recon_persistent(const SweepParams &p, int conn, int queue, i
 }
 
 // --------------------------------------------------------------- output
-// out = R (cropped to H x W); optionally bin = (R < threshold).
+// out = R (cropped to H x W); optionally bin = (R < threshold). One row per
+// blockIdx.y, 16 columns per thread.
 __global__ void recon_out_kernel(const uint8_t *Rw, int Wp, uint8_t *out, int64_t ld_out, int H, int W,
                                  uint8_t *bin, int64_t ld_bin, int threshold)
 {
     const int r = blockIdx.y;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < W; c += gridDim.x * blockDim.x) {
-        const uint8_t v = Rw[(int64_t)r * Wp + c];
-        if (out) out[(int64_t)r * ld_out + c] = v;
-        if (bin) bin[(int64_t)r * ld_bin + c] = v < threshold ? 1 : 0;
+    const int c0 = (blockIdx.x * blockDim.x + threadIdx.x) * 16;
+    if (c0 >= W) return;
+    const int n = min(16, W - c0);
+    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(Rw + (int64_t)r * Wp + c0));
+    if (out) store16(out + (int64_t)r * ld_out + c0, v, n);
+    if (bin) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        uint32_t o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x |= (uint32_t)((int)((w[q] >> (8 * k)) & 0xffu) < threshold) << (8 * k);
+            o[q] = x;
+        }
+        store16(bin + (int64_t)r * ld_bin + c0, make_uint4(o[0], o[1], o[2], o[3]), n);
     }
 }
 
 cudaError_t launch_recon_out(const uint8_t *Rw, int Wp, uint8_t *out, int64_t ld_out, int H, int W,
                              uint8_t *bin, int64_t ld_bin, int threshold, cudaStream_t s)
 {
-    recon_out_kernel<<<dim3((unsigned)ceil_div(W, 256), (unsigned)H), 256, 0, s>>>(Rw, Wp, out, ld_out, H, W,
-                                                                                  bin, ld_bin, threshold);
+    const int threads = 128;
+    recon_out_kernel<<<dim3((unsigned)ceil_div(ceil_div(W, 16), threads), (unsigned)H), threads, 0, s>>>(
+        Rw, Wp, out, ld_out, H, W, bin, ld_bin, threshold);
     return cudaGetLastError();
 }
 
