@@ -165,6 +165,7 @@ void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w, bool grouped = false)
         ReconImage &d = b.img[i];
         d.Rw = cv.take<uint8_t>((size_t)d.Hp * d.Wp);
         d.Iw = cv.take<uint8_t>((size_t)d.Hp * d.Wp);
+        d.Cw = cv.take<uint8_t>((size_t)d.tiles_x * d.tiles_y * kEdgeBytes);
     }
 }
 

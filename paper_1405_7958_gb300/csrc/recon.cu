@@ -133,6 +133,10 @@ __global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t 
     const int64_t o = (int64_t)r * d.Wp + c0;   // Wp is a multiple of 64 and the buffers 256-byte aligned
     *reinterpret_cast<uint4 *>(d.Iw + o) = iv;
     *reinterpret_cast<uint4 *>(d.Rw + o) = rv;
+    // a tile's first column starts a 16-column chunk, its last column ends one
+    const int lt = (c0 / kTW) * d.tiles_y + r / kTH;
+    if (c0 % kTW == 0) d.Cw[(int64_t)lt * kEdgeBytes + r % kTH] = (uint8_t)rv.x;
+    if (c0 % kTW == kTW - 16) d.Cw[(int64_t)lt * kEdgeBytes + kTH + r % kTH] = (uint8_t)(rv.w >> 24);
 }
 
 cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
@@ -233,6 +237,28 @@ __device__ __forceinline__ const ReconImage &find_image(const SweepParams &p, in
     return p.b.img[k];
 }
 
+// Halo columns of tile (tx, ty) from the neighbours' edge columns: hl for
+// lane i = pixel (row i, column -1), hr = (row i, column kTW); the corners
+// (rows -1 and kTH) come from the diagonal neighbours. Zero outside the
+// padded image, like the padding itself.
+struct Halo {
+    uint32_t hl, hr, corner;   // corner: lane 0 (-1,-1), 1 (kTH,-1), 2 (-1,kTW), 3 (kTH,kTW)
+};
+__device__ __forceinline__ Halo load_halo(const ReconImage &d, int lt, int ty, int tx, int lane)
+{
+    const int ny = d.tiles_y, nx = d.tiles_x;
+    const uint8_t *C = d.Cw;
+    Halo h;
+    h.hl = tx > 0 ? __ldcg(C + (int64_t)(lt - ny) * kEdgeBytes + kTH + lane) : 0u;
+    h.hr = tx + 1 < nx ? __ldcg(C + (int64_t)(lt + ny) * kEdgeBytes + lane) : 0u;
+    h.corner = 0u;
+    if (lane == 0 && tx > 0 && ty > 0) h.corner = __ldcg(C + (int64_t)(lt - ny - 1) * kEdgeBytes + 2 * kTH - 1);
+    if (lane == 1 && tx > 0 && ty + 1 < ny) h.corner = __ldcg(C + (int64_t)(lt - ny + 1) * kEdgeBytes + kTH);
+    if (lane == 2 && tx + 1 < nx && ty > 0) h.corner = __ldcg(C + (int64_t)(lt + ny - 1) * kEdgeBytes + kTH - 1);
+    if (lane == 3 && tx + 1 < nx && ty + 1 < ny) h.corner = __ldcg(C + (int64_t)(lt + ny + 1) * kEdgeBytes);
+    return h;
+}
+
 struct WarpBuf {
     uint32_t *sRT, *sIT;   // kTH rows x kTS words: transposed R, I (u16x2 per word)
     uint32_t *sHL, *sHR;   // halo columns, index i <-> tile row i - 1
@@ -260,15 +286,11 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
     }
     const uint32_t topw = r0 > 0 ? widen2(__ldcg(Rg - ws)) : 0u;
     const uint32_t botw = r0 + kTH < d.Hp ? widen2(__ldcg(Rg + kTH * ws)) : 0u;
-    for (int i = lane; i < kTH + 2; i += 32) {
-        const int r = r0 - 1 + i;
-        uint32_t hl = 0, hr = 0;
-        if (r >= 0 && r < d.Hp) {
-            if (c0 > 0) hl = __ldcg(d.Rw + (int64_t)r * Wp + c0 - 1);
-            if (c0 + kTW < Wp) hr = __ldcg(d.Rw + (int64_t)r * Wp + c0 + kTW);
-        }
-        wb.sHL[i] = hl;
-        wb.sHR[i] = hr;
+    {
+        const Halo h = load_halo(d, lt, ty, tx, lane);
+        wb.sHL[lane + 1] = h.hl;
+        wb.sHR[lane + 1] = h.hr;
+        if (lane < 4) ((lane & 2) ? wb.sHR : wb.sHL)[(lane & 1) ? kTH + 1 : 0] = h.corner;
     }
     __syncwarp();
 
@@ -381,6 +403,17 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
         if (r == kTH - 1) dbot = diff;
     }
     if (!__any_sync(0xffffffffu, any != 0)) return (uint32_t)it;
+    // edge columns: lane 0 holds column 0 (low halves), lane 31 column kTW - 1
+    if ((lane == 0 && dl) || (lane == 31 && dr)) {
+        uint32_t *ce = reinterpret_cast<uint32_t *>(d.Cw + (int64_t)lt * kEdgeBytes + (lane ? kTH : 0));
+#pragma unroll
+        for (int q = 0; q < kTH / 4; ++q) {
+            uint32_t wv = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) wv |= ((lane ? R[4 * q + k] >> 16 : R[4 * q + k]) & 0xffu) << (8 * k);
+            __stcg(ce + q, wv);
+        }
+    }
     const bool top = __any_sync(0xffffffffu, dtop != 0);
     const bool bot = __any_sync(0xffffffffu, dbot != 0);
     const bool left = __shfl_sync(0xffffffffu, dl, 0) != 0;
@@ -447,15 +480,11 @@ __device__ __forceinline__ uint32_t visit_queue(const SweepParams &p, int t, uin
         qb.R[i * kQW + 1 + 2 * lane] = w & 0xffu;
         qb.R[i * kQW + 2 + 2 * lane] = w >> 8;
     }
-    for (int i = lane; i < kTH + 2; i += 32) {
-        const int r = r0 - 1 + i;
-        uint32_t hl = 0, hr = 0;
-        if (r >= 0 && r < d.Hp) {
-            if (c0 > 0) hl = __ldcg(d.Rw + (int64_t)r * Wp + c0 - 1);
-            if (c0 + kTW < Wp) hr = __ldcg(d.Rw + (int64_t)r * Wp + c0 + kTW);
-        }
-        qb.R[i * kQW] = hl;
-        qb.R[i * kQW + kQW - 1] = hr;
+    {
+        const Halo h = load_halo(d, lt, ty, tx, lane);
+        qb.R[(lane + 1) * kQW] = h.hl;
+        qb.R[(lane + 1) * kQW + kQW - 1] = h.hr;
+        if (lane < 4) qb.R[((lane & 1) ? kTH + 1 : 0) * kQW + ((lane & 2) ? kQW - 1 : 0)] = h.corner;
     }
     for (int r = 0; r < kTH; ++r)
         reinterpret_cast<uint16_t *>(qb.I + r * kTW)[lane] =
@@ -534,6 +563,10 @@ __device__ __forceinline__ uint32_t visit_queue(const SweepParams &p, int t, uin
         if (r == kTH - 1) dbot = diff;
     }
     if (!__any_sync(0xffffffffu, any != 0)) return pops;
+    // edge columns, lane = row
+    if (__shfl_sync(0xffffffffu, dl, 0)) d.Cw[(int64_t)lt * kEdgeBytes + lane] = (uint8_t)vR[(lane + 1) * kQW + 1];
+    if (__shfl_sync(0xffffffffu, dr, 31))
+        d.Cw[(int64_t)lt * kEdgeBytes + kTH + lane] = (uint8_t)vR[(lane + 1) * kQW + kTW];
     const bool top = __any_sync(0xffffffffu, dtop != 0);
     const bool bot = __any_sync(0xffffffffu, dbot != 0);
     const bool left = __shfl_sync(0xffffffffu, dl, 0) != 0;

@@ -8,6 +8,10 @@ namespace rtk {
 
 constexpr int kTH = 32;       // warp tile: 32 rows
 constexpr int kTW = 64;       //            x 64 columns (2 per lane)
+// The first and last column of every tile are also kept contiguously (32
+// bytes each) so that a visit reads its left and right halo in one sector
+// each instead of one sector per row.
+constexpr int kEdgeBytes = 2 * kTH;
 
 // One image of a reconstruction batch. The kernels work on padded copies
 // (Iw = mask, Rw = running reconstruction) of Hp x Wp pixels (multiples of
@@ -20,6 +24,7 @@ struct ReconImage {
     int64_t ld_mask;
     uint8_t *Rw;
     uint8_t *Iw;
+    uint8_t *Cw;            // per tile (local index), kEdgeBytes: its first and last column of Rw
     int H, W, Hp, Wp;
     int tiles_x, tiles_y;
     int tile_base;          // index of this image's first tile in the batch
