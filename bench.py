@@ -31,6 +31,14 @@ UNIT = "tiles/s"
 BYTES_CHAIN = 9          # compulsory bytes/px: input 1 + labels 4 + EDT 4
 BYTES_RF = 2             # R and F outputs, 1 byte each
 BYTES_RECON = 2          # reconstruction: read mask 1, write R 1
+BYTES_PASS = 3           # one directional raster pass over a pixel: read R and I, write R
+PASSES_PER_ITERATION = 3 # a dense tile iteration: down, up and row passes
+TILE_PX = 32 * 64        # pixels of one warp tile
+# ncu summary of the propagation kernel on the bench workload: its DRAM
+# traffic per launch is reported while the kernel sources still hash to the
+# value recorded there (else traffic is null: the counters are stale)
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "recon_persistent_8x4k.md")
+KERNEL_SOURCES = ("paper_1405_7958_gb300/csrc/recon.cu", "paper_1405_7958_gb300/csrc/recon.cuh")
 
 
 def parse():
@@ -60,6 +68,36 @@ def make_tiles(n, rank, size):
     workers = max(1, min(n, os.cpu_count() or 1))
     with mp.get_context("spawn").Pool(workers) as pool:
         return pool.map(_gen, seeds)
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the propagation kernel from its committed ncu
+    summary, or None when the summary is missing or the kernel has changed."""
+    try:
+        with open(TRAFFIC_PROFILE) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    fields = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    try:
+        if fields.get("kernel sources sha256/16") != kernel_hash():
+            return None
+        return int(fields["dram bytes per launch (read + write)"])
+    except (KeyError, ValueError):
+        return None
 
 
 def load_peaks():
@@ -286,9 +324,13 @@ def run_native(a, rank, world, local_rank):
         per_launch_s = sweep_ms / sweep_n / 1000.0
         algo_bytes = BYTES_RECON * px * a.batch
         ach = algo_bytes / per_launch_s / 1e9
+        its = visits[1]       # dense tile iterations of one step (taken after the warm-up)
+        pass_bytes = its * PASSES_PER_ITERATION * TILE_PX * BYTES_PASS
         roof = {"kernel": "recon_persistent_kernel<8,0>", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
-                "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": per_launch_s * 1000}
+                "frac": ach / peak, "peak_source": peak_kind, "traffic": profiled_traffic(),
+                "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": per_launch_s * 1000,
+                "pass_bytes_per_launch": pass_bytes, "pass_equivalent_gbs": pass_bytes / per_launch_s / 1e9,
+                "pass_equivalent_frac": pass_bytes / per_launch_s / 1e9 / peak}
 
     # end to end through the public API with host buffers
     e2e = None

@@ -17,7 +17,7 @@ import torch
 
 import paper_1405_7958_gb300 as rt
 
-CANDIDATES = tuple((v, m) for v in (rt.RT_RASTER,) for m in (2, 4, 8, 16)) + ((rt.RT_HYBRID, 0),)
+CANDIDATES = tuple((v, m) for v in (rt.RT_RASTER,) for m in (4, 8, 12, 16)) + ((rt.RT_HYBRID, 0),)
 
 
 def size_class(images) -> str:

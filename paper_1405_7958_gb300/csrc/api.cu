@@ -207,7 +207,7 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
             p.nvirt = w.ctl + kCtlGroupCount + g;
             p.pending = w.ctl + kCtlGroupPending + g;
         }
-        p.max_local = max_local > 0 ? max_local : (v == RT_HYBRID ? 64 : 8);
+        p.max_local = max_local > 0 ? max_local : (v == RT_HYBRID ? 64 : 12);
         if (v == RT_HYBRID) {
             RT_CUDA_TRY(launch_recon_dense(p, conn, s));
             ctx->launches += 1;

@@ -310,8 +310,12 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
             if (CONN == 8) {
                 uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
                 uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
-                if (lane == 0) sl = wb.sHL[r] << 16;
-                if (lane == 31) sr = wb.sHR[r];
+                // indexed through prev (whose top bit is always clear) so that the
+                // loads stay in the loop instead of being hoisted into registers
+                const int hi_ = r + (int)(prev >> 31);
+                const uint32_t hl = wb.sHL[hi_], hr = wb.sHR[hi_];
+                sl = lane == 0 ? hl << 16 : sl;
+                sr = lane == 31 ? hr : sr;
                 m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
             }
             const uint32_t nv = vmin2(m, Is[r * kTS]);
@@ -333,8 +337,10 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
             if (CONN == 8) {
                 uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
                 uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
-                if (lane == 0) sl = wb.sHL[r + 2] << 16;
-                if (lane == 31) sr = wb.sHR[r + 2];
+                const int hi_ = r + 2 + (int)(prev >> 31);
+                const uint32_t hl = wb.sHL[hi_], hr = wb.sHR[hi_];
+                sl = lane == 0 ? hl << 16 : sl;
+                sr = lane == 31 ? hr : sr;
                 m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
             }
             const uint32_t nv = vmin2(m, Is[r * kTS]);
@@ -355,17 +361,15 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
         {
             uint32_t *row = wb.sRT + lane * kTS;
             const uint32_t *irow = wb.sIT + lane * kTS;
-            uint32_t x = wb.sHL[lane + 1];
+            uint32_t x = wb.sHL[lane + 1], hd = 0;
 #pragma unroll 8
             for (int j = 0; j < kTW / 2; ++j) {
                 const uint32_t w = row[j], iw = irow[j];
                 const uint32_t a = min(max(w & 0xffffu, x), iw & 0xffffu);
                 x = min(max(w >> 16, a), iw >> 16);
                 const uint32_t nw = a | (x << 16);
-                if (nw != w) {
-                    row[j] = nw;
-                    ch = true;
-                }
+                row[j] = nw;
+                hd |= nw ^ w;
             }
             x = wb.sHR[lane + 1];
 #pragma unroll 8
@@ -374,11 +378,10 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
                 const uint32_t b = min(max(w >> 16, x), iw >> 16);
                 x = min(max(w & 0xffffu, b), iw & 0xffffu);
                 const uint32_t nw = x | (b << 16);
-                if (nw != w) {
-                    row[j] = nw;
-                    ch = true;
-                }
+                row[j] = nw;
+                hd |= nw ^ w;
             }
+            ch = hd != 0;
         }
         __syncwarp();
 #pragma unroll
@@ -671,7 +674,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 5) recon_persis
         if (lane == 0) pend = ld_acquire(p.pending);
         pend = __shfl_sync(0xffffffffu, pend, 0);
         if (pend == 0) break;
-        if (++idle > 4) __nanosleep(100);
+        if (++idle > 4) __nanosleep(1500);
         int late = 0;
         if (lane == 0 && (idle & 63) == 0) late = globaltimer_ns() - t_start > p.timeout_ns;
         if (__shfl_sync(0xffffffffu, late, 0)) {
