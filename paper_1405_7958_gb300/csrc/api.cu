@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "edt.cuh"
 #include "features.cuh"
+#include "fill.cuh"
 #include "mlp.cuh"
 #include "recon.cuh"
 #include "synth.cuh"
@@ -436,23 +437,34 @@ rt_status rt_fill_holes(rt_ctx *ctx, const uint8_t *in, int64_t ld_in, uint8_t *
     if ((const void *)in == (const void *)out && ld_in != ld_out) return RT_EINVAL;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    UfArgs a;
     Carve cv;
-    carve_uf(cv, a, H, W);
+    auto layout = [&](Carve &c, char *&fws, uint32_t *&flags, uint32_t *&pend, int32_t *&err) {
+        fws = c.take<char>(fill_image_bytes(H, W));
+        flags = c.take<uint32_t>((size_t)(ceil_div(H, kFillTH) * ceil_div(W, kFillTW)));
+        pend = c.take<uint32_t>(1);
+        err = c.take<int32_t>(1);
+    };
+    char *fws;
+    uint32_t *flags, *pend;
+    int32_t *err;
+    layout(cv, fws, flags, pend, err);
     rt_status st = ensure_ws(ctx, cv.off);
     if (st != RT_OK) return st;
     cv = Carve();
     cv.base = (char *)ctx->ws;
-    carve_uf(cv, a, H, W);
-    a.in = in;
-    a.ld_in = ld_in;
-    a.H = H;
-    a.W = W;
+    layout(cv, fws, flags, pend, err);
     if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
+    FillBatch fb;
+    fb.n = 0;
+    fill_add(fb, in, ld_in, out, ld_out, H, W, fws);
+    fb.conn = conn;
+    fb.flags = flags;
+    fb.pending = pend;
+    fb.err = dev_status ? dev_status : err;
+    fb.timeout_ns = kSweepTimeoutNs;
     Phase ph(ctx, RT_PHASE_FILL, s);
-    ctx->launches += 4;
-    RT_CUDA_TRY(uf_build(a, conn, kFgZero, false, true, s));
-    return cuda_status(uf_fill_out(a, conn, out, ld_out, s));
+    ctx->launches += 3;
+    return cuda_status(launch_fill(fb, ctx->num_sms, s));
 }
 
 rt_status rt_label_area(rt_ctx *ctx, const uint8_t *bin, int64_t ld_bin, int32_t *labels, int64_t ld_lab, int H,
@@ -689,7 +701,9 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         FeatBatch fb;
         float *feat = nullptr;
         int32_t *picks_dev = nullptr;
-        auto layout = [&](Carve &cv, ReconWs &w, std::vector<uint8_t *> &Bs, uint8_t *&Fw, char *&uf_ws,
+        std::vector<char *> fill_ws;
+        uint32_t *fill_flags = nullptr, *fill_pending = nullptr;
+        auto layout = [&](Carve &cv, ReconWs &w, std::vector<uint8_t *> &Bs, char *&uf_ws,
                           char *&edt_ws) {
             carve_recon(cv, b, w, learned);
             if (learned) {
@@ -712,22 +726,28 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
             }
             Bs.resize(cn);
             for (int i = 0; i < cn; ++i) Bs[i] = cv.take<uint8_t>((size_t)b.img[i].H * b.img[i].W);
-            Fw = cv.take<uint8_t>((size_t)maxN);
             // union-find pieces sized for (maxH, maxW), enough for every tile of the chunk
             uf_ws = cv.take<char>(uf_workspace_bytes(maxH, maxW));
             edt_ws = cv.take<char>(edt_workspace_bytes(maxH, maxW) + (size_t)maxN * 2);
+            fill_ws.resize(cn);
+            int fill_tiles = 0;
+            for (int i = 0; i < cn; ++i) {
+                fill_ws[i] = cv.take<char>(fill_image_bytes(b.img[i].H, b.img[i].W));
+                fill_tiles += (int)(ceil_div(b.img[i].H, kFillTH) * ceil_div(b.img[i].W, kFillTW));
+            }
+            fill_flags = cv.take<uint32_t>((size_t)fill_tiles);
+            fill_pending = cv.take<uint32_t>(1);
         };
         Carve cv;
         ReconWs w;
         std::vector<uint8_t *> Bs;
-        uint8_t *Fw;
         char *uf_ws, *edt_ws;
-        layout(cv, w, Bs, Fw, uf_ws, edt_ws);
+        layout(cv, w, Bs, uf_ws, edt_ws);
         rt_status st = ensure_ws(ctx, cv.off);
         if (st != RT_OK) return st;
         cv = Carve();
         cv.base = (char *)ctx->ws;
-        layout(cv, w, Bs, Fw, uf_ws, edt_ws);
+        layout(cv, w, Bs, uf_ws, edt_ws);
 
         RT_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
         if (!learned) {
@@ -755,29 +775,40 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         for (int i = 0; i < cn; ++i) {
             const rt_tile &t = tiles[c0 + i];
             const ReconImage &d = b.img[i];
-            const int H = t.H, W = t.W;
-            {
-                Phase ph(ctx, RT_PHASE_RECON_OUT, s);
-                ctx->launches += 1;
-                RT_CUDA_TRY(launch_recon_out(d.Rw, d.Wp, t.recon, t.ld_recon, H, W, Bs[i], W, P.threshold, s));
+            Phase ph(ctx, RT_PHASE_RECON_OUT, s);
+            ctx->launches += 1;
+            RT_CUDA_TRY(launch_recon_out(d.Rw, d.Wp, t.recon, t.ld_recon, t.H, t.W, Bs[i], t.W, P.threshold, s));
+        }
+        // hole filling for the whole chunk at once; F replaces the binary
+        // image unless the caller wants F in its own buffer
+        {
+            FillBatch fb_;
+            fb_.n = 0;
+            for (int i = 0; i < cn; ++i) {
+                const rt_tile &t = tiles[c0 + i];
+                uint8_t *F = t.filled ? t.filled : Bs[i];
+                fill_add(fb_, Bs[i], t.W, F, t.filled ? t.ld_filled : t.W, t.H, t.W, fill_ws[i]);
             }
-            UfArgs fa;
+            fb_.conn = P.conn_fill;
+            fb_.flags = fill_flags;
+            fb_.pending = fill_pending;
+            fb_.err = w.err;
+            fb_.timeout_ns = kSweepTimeoutNs;
+            Phase ph(ctx, RT_PHASE_FILL, s);
+            ctx->launches += 3;
+            RT_CUDA_TRY(launch_fill(fb_, ctx->num_sms, s));
+        }
+        for (int i = 0; i < cn; ++i) {
+            const rt_tile &t = tiles[c0 + i];
+            const int H = t.H, W = t.W;
+            const uint8_t *F = t.filled ? t.filled : Bs[i];
+            const int64_t ldF = t.filled ? t.ld_filled : W;
+            UfArgs la;
             Carve uc;
             uc.base = uf_ws;
-            carve_uf(uc, fa, H, W);
-            fa.in = Bs[i];
-            fa.ld_in = W;
-            fa.H = H;
-            fa.W = W;
-            uint8_t *F = t.filled ? t.filled : Fw;
-            const int64_t ldF = t.filled ? t.ld_filled : W;
-            {
-                Phase ph(ctx, RT_PHASE_FILL, s);
-                ctx->launches += 4;
-                RT_CUDA_TRY(uf_build(fa, P.conn_fill, kFgZero, false, true, s));
-                RT_CUDA_TRY(uf_fill_out(fa, P.conn_fill, F, ldF, s));
-            }
-            UfArgs la = fa;
+            carve_uf(uc, la, H, W);
+            la.H = H;
+            la.W = W;
             la.in = F;
             la.ld_in = ldF;
             if (t.n_kept) RT_CUDA_TRY(cudaMemsetAsync(t.n_kept, 0, sizeof(int32_t), s));

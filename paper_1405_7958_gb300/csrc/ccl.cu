@@ -1,4 +1,4 @@
-// BWLabel (Section 5.1) and FillHoles (Sections 3.2.1, 5.1) by union-find.
+// BWLabel (Section 5.1) by union-find.
 //
 // The paper's BWLabel follows the union-find pattern: every pixel starts as
 // its own tree, trees of adjacent foreground pixels are merged, and labels
@@ -14,9 +14,8 @@
 //   2. local roots of pixels that touch across a block edge are merged in
 //      global memory (only those roots are nodes of the global forest);
 //   3. every listed local root is pointed at its final root, to which it adds
-//      its area (labeling) or its border flag (hole filling: the components
-//      are the background's, and those that never touch the border are the
-//      holes);
+//      its area (or its border-contact flag, for the components of the
+//      complement);
 //   4. the output pass labels each block again in shared memory (the local
 //      roots come out identical) and maps every pixel through its local
 //      root's final root.
@@ -344,34 +343,6 @@ cudaError_t uf_labels_out(const UfArgs &a, int conn, int32_t *labels, int64_t ld
     const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
     if (conn == 8) uf_labels_kernel<8><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
     else uf_labels_kernel<4><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
-    return cudaGetLastError();
-}
-
-// 4b. hole filling from the background components
-template <int CONN>
-__global__ void __launch_bounds__(kThreads) uf_fill_kernel(UfArgs a, uint8_t *out, int64_t ld_out)
-{
-    __shared__ int P[kB * kB];
-    __shared__ uint32_t M[kB];
-    int roots[kRowsPerThread];
-    local_labels<CONN>(a, kFgZero, P, M, roots);
-    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB, c = c0 + tx;
-#pragma unroll
-    for (int k = 0; k < kRowsPerThread; ++k) {
-        const int r = r0 + w * kRowsPerThread + k;
-        if (r >= a.H || c >= a.W) continue;
-        uint8_t v = 1;   // foreground
-        if (roots[k] >= 0) v = a.A[a.U[global_index(a, roots[k])]] ? 0 : 1;
-        out[(int64_t)r * ld_out + c] = v;
-    }
-}
-
-cudaError_t uf_fill_out(const UfArgs &a, int conn, uint8_t *out, int64_t ld_out, cudaStream_t s)
-{
-    const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
-    if (conn == 8) uf_fill_kernel<8><<<grid_blk, kThreads, 0, s>>>(a, out, ld_out);
-    else uf_fill_kernel<4><<<grid_blk, kThreads, 0, s>>>(a, out, ld_out);
     return cudaGetLastError();
 }
 

@@ -1,4 +1,4 @@
-// Union-find connected components on the GPU (labeling and hole filling).
+// Union-find connected components on the GPU (BWLabel).
 #pragma once
 
 #include "common.cuh"
@@ -6,7 +6,7 @@
 namespace rtk {
 
 // How the binary input is read: foreground = (byte != 0), or the complement
-// (background components, used by hole filling).
+// (the components of the background).
 enum UfSource { kFgNonzero = 0, kFgZero = 1 };
 
 constexpr int kUfBlock = 32;       // block side
@@ -35,7 +35,5 @@ cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, boo
 // labels = root if fg and min_area <= area(root) <= max_area, else -1
 cudaError_t uf_labels_out(const UfArgs &a, int conn, int32_t *labels, int64_t ld_lab, int32_t min_area,
                           int32_t max_area, int32_t *n_kept, cudaStream_t s);
-// out = 1 where in != 0 or the background component does not touch the border
-cudaError_t uf_fill_out(const UfArgs &a, int conn, uint8_t *out, int64_t ld_out, cudaStream_t s);
 
 }  // namespace rtk
