@@ -493,7 +493,7 @@ rt_status rt_label_area(rt_ctx *ctx, const uint8_t *bin, int64_t ld_bin, int32_t
     Phase ph(ctx, RT_PHASE_LABEL, s);
     ctx->launches += 4;
     RT_CUDA_TRY(uf_build(a, conn, kFgNonzero, true, false, s));
-    return cuda_status(uf_labels_out(a, conn, labels, ld_lab, min_area, max_area, dev_n_kept, s));
+    return cuda_status(uf_labels_out(a, conn, labels, ld_lab, min_area, max_area, dev_n_kept, nullptr, s));
 }
 
 rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int64_t ld_d2, int H, int W,
@@ -512,6 +512,7 @@ rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int
     EdtArgs a;
     a.fg8 = fg;
     a.lab32 = nullptr;
+    a.bits = nullptr;
     a.ld_in = ld_fg;
     a.H = H;
     a.W = W;
@@ -703,6 +704,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         int32_t *picks_dev = nullptr;
         std::vector<char *> fill_ws;
         uint32_t *fill_flags = nullptr, *fill_pending = nullptr;
+        uint32_t *kept_bits = nullptr;   // kept pixels of the tile being labeled, for its distance transform
         auto layout = [&](Carve &cv, ReconWs &w, std::vector<uint8_t *> &Bs, char *&uf_ws,
                           char *&edt_ws) {
             carve_recon(cv, b, w, learned);
@@ -736,6 +738,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
                 fill_tiles += (int)(ceil_div(b.img[i].H, kFillTH) * ceil_div(b.img[i].W, kFillTW));
             }
             fill_flags = cv.take<uint32_t>((size_t)fill_tiles);
+            kept_bits = cv.take<uint32_t>((size_t)maxH * ceil_div(maxW, 32));
             fill_pending = cv.take<uint32_t>(1);
         };
         Carve cv;
@@ -816,11 +819,12 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
                 Phase ph(ctx, RT_PHASE_LABEL, s);
                 ctx->launches += 4;
                 RT_CUDA_TRY(uf_build(la, 8, kFgNonzero, true, false, s));
-                RT_CUDA_TRY(uf_labels_out(la, 8, t.labels, t.ld_labels, P.min_area, P.max_area, t.n_kept, s));
+                RT_CUDA_TRY(uf_labels_out(la, 8, t.labels, t.ld_labels, P.min_area, P.max_area, t.n_kept, kept_bits, s));
             }
             EdtArgs ea;
             ea.fg8 = nullptr;
-            ea.lab32 = t.labels;
+            ea.lab32 = nullptr;
+            ea.bits = kept_bits;
             ea.ld_in = t.ld_labels;
             ea.H = H;
             ea.W = W;

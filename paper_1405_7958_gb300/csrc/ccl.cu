@@ -134,6 +134,7 @@ __device__ __forceinline__ void local_labels(const UfArgs &a, int source, int *P
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
     const int c = c0 + tx;
+    uint32_t any = 0;
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int lr = w * kRowsPerThread + k;
@@ -145,8 +146,14 @@ __device__ __forceinline__ void local_labels(const UfArgs &a, int source, int *P
         int v = -1;
         if (f) v = lr * kB + (31 - __clz(starts & (0xffffffffu >> (31 - tx))));
         P[lr * kB + tx] = v;
+        any |= m;
     }
-    __syncthreads();
+    // a block without foreground (most of a sparse mask) has nothing to join
+    if (!__syncthreads_or(any != 0)) {
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) roots[k] = -1;
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int lr = w * kRowsPerThread + k;
@@ -309,10 +316,12 @@ cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, boo
     return cudaGetLastError();
 }
 
-// 4a. labels with the area filter
+// 4a. labels with the area filter; optionally the kept pixels as a bit
+// plane (bit c % 32 of word r * ceil(W / 32) + c / 32), which is all the
+// distance transform needs to read
 template <int CONN>
 __global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfArgs a, int32_t *labels, int64_t ld_lab, int32_t amin,
-                                                        int32_t amax, int32_t *n_kept)
+                                                        int32_t amax, int32_t *n_kept, uint32_t *fgbits)
 {
     __shared__ int P[kB * kB];
     __shared__ uint32_t M[kB];
@@ -320,12 +329,13 @@ __global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfArgs a, int32_t *
     local_labels<CONN>(a, kFgNonzero, P, M, roots);
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB, c = c0 + tx;
+    const int64_t wpr = ceil_div(a.W, 32);
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int r = r0 + w * kRowsPerThread + k;
-        if (r >= a.H || c >= a.W) continue;
+        const bool in = r < a.H && c < a.W;
         int32_t out = -1;
-        if (roots[k] >= 0) {
+        if (in && roots[k] >= 0) {
             const int32_t root = a.U[global_index(a, roots[k])];
             const int32_t area = a.A[root];
             if (area >= amin && area <= amax) {
@@ -333,16 +343,22 @@ __global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfArgs a, int32_t *
                 if (n_kept && root == (int32_t)((int64_t)r * a.W + c)) atomicAdd(n_kept, 1);
             }
         }
-        labels[(int64_t)r * ld_lab + c] = out;
+        if (in) labels[(int64_t)r * ld_lab + c] = out;
+        if (fgbits) {
+            const uint32_t bits = __ballot_sync(0xffffffffu, out >= 0);
+            if (tx == 0 && r < a.H) fgbits[(int64_t)r * wpr + blockIdx.x] = bits;
+        }
     }
 }
 
 cudaError_t uf_labels_out(const UfArgs &a, int conn, int32_t *labels, int64_t ld_lab, int32_t min_area,
-                          int32_t max_area, int32_t *n_kept, cudaStream_t s)
+                          int32_t max_area, int32_t *n_kept, uint32_t *fgbits, cudaStream_t s)
 {
     const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
-    if (conn == 8) uf_labels_kernel<8><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
-    else uf_labels_kernel<4><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept);
+    if (conn == 8)
+        uf_labels_kernel<8><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept, fgbits);
+    else
+        uf_labels_kernel<4><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept, fgbits);
     return cudaGetLastError();
 }
 

@@ -32,8 +32,9 @@ size_t uf_workspace_bytes(int H, int W);
 // or border-contact flag (flag_border).
 cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, bool flag_border,
                      cudaStream_t s);
-// labels = root if fg and min_area <= area(root) <= max_area, else -1
+// labels = root if fg and min_area <= area(root) <= max_area, else -1; with
+// fgbits, also the bit plane of labels >= 0 (ceil(W / 32) words per row)
 cudaError_t uf_labels_out(const UfArgs &a, int conn, int32_t *labels, int64_t ld_lab, int32_t min_area,
-                          int32_t max_area, int32_t *n_kept, cudaStream_t s);
+                          int32_t max_area, int32_t *n_kept, uint32_t *fgbits, cudaStream_t s);
 
 }  // namespace rtk

@@ -29,6 +29,7 @@ size_t edt_workspace_bytes(int H, int W)
 
 __device__ __forceinline__ bool edt_is_bg(const EdtArgs &a, int r, int c)
 {
+    if (a.bits) return !((a.bits[(int64_t)r * ceil_div(a.W, 32) + (c >> 5)] >> (c & 31)) & 1u);
     if (a.lab32) return a.lab32[(int64_t)r * a.ld_in + c] < 0;
     return a.fg8[(int64_t)r * a.ld_in + c] == 0;
 }
@@ -93,7 +94,13 @@ __global__ void edt_row_kernel(EdtArgs a)
     extern __shared__ uint16_t sg[];
     const int r = blockIdx.x;
     const uint16_t *grow = a.g + (int64_t)r * a.W;
-    for (int c = threadIdx.x; c < a.W; c += blockDim.x) sg[c] = grow[c];
+    if ((a.W & 7) == 0) {   // rows 16-byte aligned: 8 values per load
+        const uint4 *src = reinterpret_cast<const uint4 *>(grow);
+        uint4 *dst = reinterpret_cast<uint4 *>(sg);
+        for (int k = threadIdx.x; k < a.W / 8; k += blockDim.x) dst[k] = __ldcs(src + k);
+    } else {
+        for (int c = threadIdx.x; c < a.W; c += blockDim.x) sg[c] = grow[c];
+    }
     __syncthreads();
     const bool any = *a.any_bg != 0;
     int32_t *out = a.d2 + (int64_t)r * a.ld_d2;

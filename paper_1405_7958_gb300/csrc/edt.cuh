@@ -5,11 +5,12 @@
 
 namespace rtk {
 
-// Foreground source: a binary byte image (fg = byte != 0) or a label image
-// (fg = label >= 0).
+// Foreground source: a binary byte image (fg = byte != 0), a label image
+// (fg = label >= 0) or a bit plane (fg = bit set; ceil(W / 32) words per row).
 struct EdtArgs {
-    const uint8_t *fg8;     // one of fg8 / lab32 is set
+    const uint8_t *fg8;     // one of fg8 / lab32 / bits is set
     const int32_t *lab32;
+    const uint32_t *bits;
     int64_t ld_in;
     int H, W;
     int32_t *d2;            // output

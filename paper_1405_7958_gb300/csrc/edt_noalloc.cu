@@ -68,6 +68,7 @@ extern "C" rt_status rt_edt_noalloc(const uint8_t *fg, int64_t ld_fg, int32_t *d
     rtk::EdtArgs a;
     a.fg8 = fg;
     a.lab32 = nullptr;
+    a.bits = nullptr;
     a.ld_in = ld_fg;
     a.H = H;
     a.W = W;
