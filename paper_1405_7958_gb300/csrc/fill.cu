@@ -259,7 +259,7 @@ __device__ __forceinline__ void fill_visit(const FillBatch &b, int tg, int lane)
 // column) and visits those flagged until nothing is flagged or being
 // visited. Cooperative launch only to make every owner resident.
 template <int CONN>
-__global__ void __launch_bounds__(kFillWarps * 32) fill_prop_kernel(FillBatch a)
+__global__ void __launch_bounds__(kFillWarps * 32, 4) fill_prop_kernel(FillBatch a)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = a.ntiles;
