@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_dense_kernel(SweepPar
 // every warp is resident (a flagged tile's owner always runs).
 // QUEUE = 0: dense visits; QUEUE = 1: queue visits.
 template <int CONN, int QUEUE>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 5) recon_persistent_kernel(SweepParams p)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persistent_kernel(SweepParams p)
 {
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
