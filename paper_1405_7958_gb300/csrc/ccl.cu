@@ -16,9 +16,8 @@
 //   3. every listed local root is pointed at its final root, to which it adds
 //      its area (or its border-contact flag, for the components of the
 //      complement);
-//   4. the output pass labels each block again in shared memory (the local
-//      roots come out identical) and maps every pixel through its local
-//      root's final root.
+//   4. the output pass maps every pixel through its local root (recorded by
+//      pass 1) to its final root.
 #include "ccl.cuh"
 
 namespace rtk {
@@ -31,7 +30,8 @@ size_t uf_workspace_bytes(int H, int W)
 {
     const size_t N = (size_t)H * W;
     const size_t nblk = (size_t)ceil_div(W, kB) * ceil_div(H, kB);
-    return 2 * N * sizeof(int32_t) + nblk * kUfEdge * sizeof(int32_t) + (N / 2 + 2) * sizeof(int32_t) + 8 * 256;
+    return 2 * N * sizeof(int32_t) + nblk * kUfEdge * sizeof(int32_t) + (N / 2 + 2) * sizeof(int32_t) +
+           N * sizeof(uint16_t) + 8 * 256;
 }
 
 __device__ __forceinline__ bool is_fg(const uint8_t *in, int64_t ld, int r, int c, int source)
@@ -211,6 +211,12 @@ __global__ void __launch_bounds__(kThreads) uf_local_kernel(UfArgs a, int source
         else if (r == 0 || c == 0 || r == a.H - 1 || c == a.W - 1) cnt[roots[k]] = 1;
     }
     __syncthreads();
+    // every pixel's local root, so that the output pass need not label the block again
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        const int r = r0 + w * kRowsPerThread + k, c = c0 + tx;
+        if (r < a.H && c < a.W) a.lroot[(int64_t)r * a.W + c] = roots[k] >= 0 ? (uint16_t)roots[k] : (uint16_t)0xFFFFu;
+    }
     int32_t *edge = a.edge + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kUfEdge;
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
@@ -316,17 +322,12 @@ cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, boo
     return cudaGetLastError();
 }
 
-// 4a. labels with the area filter; optionally the kept pixels as a bit
-// plane (bit c % 32 of word r * ceil(W / 32) + c / 32), which is all the
-// distance transform needs to read
-template <int CONN>
+// 4a. labels with the area filter, from every pixel's local root (recorded
+// by pass 1); optionally the kept pixels as a bit plane (bit c % 32 of word
+// r * ceil(W / 32) + c / 32), which is all the distance transform needs
 __global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfArgs a, int32_t *labels, int64_t ld_lab, int32_t amin,
                                                         int32_t amax, int32_t *n_kept, uint32_t *fgbits)
 {
-    __shared__ int P[kB * kB];
-    __shared__ uint32_t M[kB];
-    int roots[kRowsPerThread];
-    local_labels<CONN>(a, kFgNonzero, P, M, roots);
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB, c = c0 + tx;
     const int64_t wpr = ceil_div(a.W, 32);
@@ -334,9 +335,10 @@ __global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfArgs a, int32_t *
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int r = r0 + w * kRowsPerThread + k;
         const bool in = r < a.H && c < a.W;
+        const uint32_t lr = in ? a.lroot[(int64_t)r * a.W + c] : 0xFFFFu;
         int32_t out = -1;
-        if (in && roots[k] >= 0) {
-            const int32_t root = a.U[global_index(a, roots[k])];
+        if (lr != 0xFFFFu) {
+            const int32_t root = a.U[global_index(a, (int)lr)];
             const int32_t area = a.A[root];
             if (area >= amin && area <= amax) {
                 out = root;
@@ -355,10 +357,8 @@ cudaError_t uf_labels_out(const UfArgs &a, int conn, int32_t *labels, int64_t ld
                           int32_t max_area, int32_t *n_kept, uint32_t *fgbits, cudaStream_t s)
 {
     const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
-    if (conn == 8)
-        uf_labels_kernel<8><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept, fgbits);
-    else
-        uf_labels_kernel<4><<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept, fgbits);
+    (void)conn;   // the components were built by uf_build with this connectivity
+    uf_labels_kernel<<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept, fgbits);
     return cudaGetLastError();
 }
 

@@ -22,9 +22,10 @@ struct UfArgs {
                          // left column, right column pixels (-1 = not in a component)
     int32_t *list;       // the local roots
     uint32_t *nlist;     // their number
+    uint16_t *lroot;     // per pixel (stride W): its local root inside its block (lr * 32 + lc), 0xFFFF = none
 };
 
-// Workspace bytes the four arrays need for an H x W image.
+// Workspace bytes the arrays need for an H x W image.
 size_t uf_workspace_bytes(int H, int W);
 
 // Builds the forest: block-local components, merges across block edges, and
