@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving leg at 800 tiles/s (0: skip)")
-    ap.add_argument("--streams", type=int, default=2, help="streams the timed steps alternate between")
+    ap.add_argument("--streams", type=int, default=3, help="streams the timed steps alternate between")
     return ap.parse_args()
 
 
@@ -373,7 +373,7 @@ def run_native(a, rank, world, local_rank):
     # so one step's copies overlap the other's kernels
     e2e = None
     if not a.no_e2e:
-        nst = 2
+        nst = max(1, a.streams)
         h_in = [torch.from_numpy(t).pin_memory() for t in tiles]
         h_L = [[torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in tiles] for _ in range(nst)]
         h_D = [[torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in tiles] for _ in range(nst)]
