@@ -18,14 +18,18 @@
 
 namespace rtk {
 
-// pass 1, CTA = 64 rows x 256 columns, thread = column: histogram (shared,
-// then global), and per 8 x 8 block the dark count and the maximum (reduced
-// over the 8 lanes of a block column)
+// pass 1, CTA = 64 rows x 256 columns, thread = column: histogram (per warp
+// in shared memory, then global), and per 8 x 8 block the dark count and the
+// maximum (reduced over the 8 lanes of a block column)
 __global__ void __launch_bounds__(256) feat_block_kernel(FeatBatch fb)
 {
-    __shared__ uint32_t sh[256];
+    // one 256-bin histogram per warp (values of neighbouring pixels cluster,
+    // so a single shared histogram would serialise on a few bins)
+    __shared__ uint32_t sh[8][256];
     const FeatImage &d = fb.img[blockIdx.z];
-    sh[threadIdx.x] = 0;
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sh[k][threadIdx.x] = 0;
     __syncthreads();
     const int c = blockIdx.x * 256 + threadIdx.x;
     const int r0 = blockIdx.y * 64;
@@ -39,7 +43,7 @@ __global__ void __launch_bounds__(256) feat_block_kernel(FeatBatch fb)
                 const int re = min(d.H, rb + 8);
                 for (int r = rb; r < re; ++r) {
                     const int v = d.img[(int64_t)r * d.ld + c];
-                    atomicAdd(sh + v, 1u);
+                    atomicAdd(&sh[warp][v], 1u);
                     dark += v < 80;
                     mx = max(mx, v);
                 }
@@ -57,7 +61,10 @@ __global__ void __launch_bounds__(256) feat_block_kernel(FeatBatch fb)
         }
     }
     __syncthreads();
-    if (sh[threadIdx.x]) atomicAdd(d.hist + threadIdx.x, sh[threadIdx.x]);
+    uint32_t tot = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tot += sh[k][threadIdx.x];
+    if (tot) atomicAdd(d.hist + threadIdx.x, tot);
 }
 
 __device__ __forceinline__ int marker_of(const uint8_t *D, int bh, int bw, int r, int c)

@@ -222,3 +222,37 @@ def test_chain_independent_of_schedule(rt):
         for k in ("R", "F", "L", "D"):
             assert np.array_equal(host(runs[0][k]), host(other[k]))
     check_chain(runs[0], I)
+
+
+def test_chain_bench_configuration(rt):
+    """The benchmark's workload exactly as it runs there: 8 distinct 4096^2
+    tiles in one batched call with the trained picker attached, on two
+    streams with one context each (consecutive calls overlap), every output of
+    every tile against the oracle."""
+    import concurrent.futures as cf
+    import os
+    from paper_1405_7958_gb300 import picker as pkmod
+    seeds = [2000 + i for i in range(8)]
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        imgs = list(ex.map(synth.config2_tile, seeds))
+        want = list(ex.map(oracle.chain, imgs))
+    d = [dev(x) for x in imgs]
+    pk = pkmod.load(os.path.join(os.path.dirname(rt.__file__), "data", "picker_config4.npz"))
+    ctxs = [rt.Context(), rt.Context()]
+    for c in ctxs:
+        pk.attach(c)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [None, None]
+    for k in range(4):
+        j = k % 2
+        with torch.cuda.stream(streams[j]):
+            outs[j] = rt.segment_batch(d, rt.SegParams(policy=1), outputs=outs[j], ctx=ctxs[j], stream=streams[j])
+    torch.cuda.synchronize()
+    for o_s in outs:
+        for o, w in zip(o_s, want):
+            assert int(host(o["status"])[0]) == 0
+            for k in ("R", "F", "L", "D"):
+                assert np.array_equal(host(o[k]), w[k])
+            assert int(host(o["n_kept"])[0]) == w["n_kept"]
+    for c in ctxs:
+        c.close()
