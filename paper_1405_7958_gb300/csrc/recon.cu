@@ -310,10 +310,10 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
             if (CONN == 8) {
                 uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
                 uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
-                // indexed through prev (whose top bit is always clear) so that the
-                // loads stay in the loop instead of being hoisted into registers
-                const int hi_ = r + (int)(prev >> 31);
-                const uint32_t hl = wb.sHL[hi_], hr = wb.sHR[hi_];
+                // volatile: the loads stay in the loop (hoisted, 64 halo words
+                // would not fit in the registers)
+                const uint32_t hl = reinterpret_cast<volatile const uint32_t *>(wb.sHL)[r];
+                const uint32_t hr = reinterpret_cast<volatile const uint32_t *>(wb.sHR)[r];
                 sl = lane == 0 ? hl << 16 : sl;
                 sr = lane == 31 ? hr : sr;
                 m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
@@ -337,8 +337,8 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
             if (CONN == 8) {
                 uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
                 uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
-                const int hi_ = r + 2 + (int)(prev >> 31);
-                const uint32_t hl = wb.sHL[hi_], hr = wb.sHR[hi_];
+                const uint32_t hl = reinterpret_cast<volatile const uint32_t *>(wb.sHL)[r + 2];
+                const uint32_t hr = reinterpret_cast<volatile const uint32_t *>(wb.sHR)[r + 2];
                 sl = lane == 0 ? hl << 16 : sl;
                 sr = lane == 31 ? hr : sr;
                 m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
