@@ -30,7 +30,7 @@ namespace rtk {
 
 constexpr int kWarpsPerCta = 4;
 constexpr int kTS = 33;                                  // transposed row stride (words)
-constexpr int kWarpWords = 2 * kTH * kTS + 2 * (kTH + 2);
+constexpr int kWarpWords = 2 * kTH * kTS + 2 * (kTH + 2) + kTH * 32 / 2;
 
 
 // ---------------------------------------------------------------- init
@@ -262,6 +262,7 @@ __device__ __forceinline__ Halo load_halo(const ReconImage &d, int lt, int ty, i
 struct WarpBuf {
     uint32_t *sRT, *sIT;   // kTH rows x kTS words: transposed R, I (u16x2 per word)
     uint32_t *sHL, *sHR;   // halo columns, index i <-> tile row i - 1
+    uint16_t *sR0;         // the tile as loaded (kTH rows x 32 lanes), for the write-back
 };
 
 // One visit of tile t by a warp. Returns after marking the tiles to visit.
@@ -281,7 +282,9 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
     const uint32_t *Is = wb.sIT + lane;   // mask, row r at Is[r * kTS]
 #pragma unroll
     for (int r = 0; r < kTH; ++r) {
-        R[r] = widen2(__ldcg(Rg + r * ws));
+        const uint16_t raw = __ldcg(Rg + r * ws);
+        wb.sR0[r * 32 + lane] = raw;
+        R[r] = widen2(raw);
         wb.sIT[r * kTS + lane] = widen2(__ldg(Ig + r * ws));
     }
     const uint32_t topw = r0 > 0 ? widen2(__ldcg(Rg - ws)) : 0u;
@@ -396,7 +399,7 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
     uint32_t dl = 0, dr = 0, dtop = 0, dbot = 0, any = 0;
 #pragma unroll
     for (int r = 0; r < kTH; ++r) {
-        const uint32_t orig = widen2(__ldcg(Rs + r * ws));
+        const uint32_t orig = widen2(wb.sR0[r * 32 + lane]);
         const uint32_t diff = orig ^ R[r];
         if (diff) __stcg(Rs + r * ws, (uint16_t)narrow2(R[r]));
         dl |= diff & 0xffffu;
@@ -599,6 +602,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_dense_kernel(SweepPar
     wb.sIT = wb.sRT + kTH * kTS;
     wb.sHL = wb.sIT + kTH * kTS;
     wb.sHR = wb.sHL + (kTH + 2);
+    wb.sR0 = reinterpret_cast<uint16_t *>(wb.sHR + (kTH + 2));
     const uint32_t it = visit_tile<CONN>(p, t, wb, lane);
     if (lane == 0 && p.visits) {
         atomicAdd(p.visits, 1u);
@@ -633,6 +637,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
         wb.sIT = wb.sRT + kTH * kTS;
         wb.sHL = wb.sIT + kTH * kTS;
         wb.sHR = wb.sHL + (kTH + 2);
+    wb.sR0 = reinterpret_cast<uint16_t *>(wb.sHR + (kTH + 2));
     }
     const int gw = blockIdx.x * kWarpsPerCta + warp;
     const int nw = gridDim.x * kWarpsPerCta;
