@@ -134,9 +134,16 @@ __device__ __forceinline__ uint32_t flood_row(uint32_t m, uint32_t s, int lane)
     return right | left;
 }
 
+// Flags tile t. `pending` is raised first (the returned count is checked,
+// which makes the increment complete before the flag is set) and lowered
+// again if the tile was already flagged, so it never undercounts.
 __device__ __forceinline__ void fill_mark(const FillBatch &b, int t)
 {
-    if (atomicOr(b.flags + t, 1u) == 0u) atomicAdd(b.pending, 1u);
+    if (atomicAdd(b.pending, 1u) == 0xffffffffu) {
+        raise_status(b.err, RT_ETIMEOUT);
+        return;
+    }
+    if (atomicOr(b.flags + t, 1u) != 0u) atomicSub(b.pending, 1u);
 }
 
 // One visit of batch tile tg by a warp.

@@ -204,30 +204,44 @@ __device__ __forceinline__ uint32_t narrow2(uint32_t w) { return __byte_perm(w, 
 // Flag bits of a tile: its halo changed, or it needs a dense visit.
 constexpr uint32_t kHalo = 1u, kDense = 2u;
 
-__device__ __forceinline__ void mark_tile(uint32_t *flags, uint32_t *pending, int t, uint32_t bits = kHalo)
+// Sets a tile's flag; returns 1 if the tile was already flagged (its visit
+// was counted before).
+__device__ __forceinline__ uint32_t mark_tile(uint32_t *flags, int t, uint32_t bits = kHalo)
 {
-    if (atomicOr(flags + t, bits) == 0u) atomicAdd(pending, 1u);
+    return atomicOr(flags + t, bits) != 0u ? 1u : 0u;
 }
 
 // Flags the neighbouring tiles that see a changed halo (and the tile itself
-// with `self_bits` when nonzero). Lane 0 only.
+// with `self_bits` when nonzero). Lane 0 only, the lane that ends the visit.
 template <int CONN>
 __device__ __forceinline__ void mark_neighbours(const SweepParams &p, const ReconImage &d, int t, int ty, int tx,
                                                 bool top, bool bot, bool left, bool right, bool tl, bool tr,
                                                 bool bl, bool br, uint32_t self_bits)
 {
     const int nx = d.tiles_x, ny = d.tiles_y;
-    if (self_bits) mark_tile(p.flags, p.pending, t, self_bits);
-    if (top && ty > 0) mark_tile(p.flags, p.pending, t - 1);
-    if (bot && ty + 1 < ny) mark_tile(p.flags, p.pending, t + 1);
-    if (left && tx > 0) mark_tile(p.flags, p.pending, t - ny);
-    if (right && tx + 1 < nx) mark_tile(p.flags, p.pending, t + ny);
-    if (CONN == 8) {
-        if (tl && ty > 0 && tx > 0) mark_tile(p.flags, p.pending, t - ny - 1);
-        if (tr && ty > 0 && tx + 1 < nx) mark_tile(p.flags, p.pending, t + ny - 1);
-        if (bl && ty + 1 < ny && tx > 0) mark_tile(p.flags, p.pending, t - ny + 1);
-        if (br && ty + 1 < ny && tx + 1 < nx) mark_tile(p.flags, p.pending, t + ny + 1);
+    const bool c[9] = {self_bits != 0, top && ty > 0, bot && ty + 1 < ny, left && tx > 0, right && tx + 1 < nx,
+                       CONN == 8 && tl && ty > 0 && tx > 0, CONN == 8 && tr && ty > 0 && tx + 1 < nx,
+                       CONN == 8 && bl && ty + 1 < ny && tx > 0, CONN == 8 && br && ty + 1 < ny && tx + 1 < nx};
+    const int u[9] = {t, t - 1, t + 1, t - ny, t + ny, t - ny - 1, t + ny - 1, t - ny + 1, t + ny + 1};
+    uint32_t nc = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) nc += c[k];
+    if (nc == 0) return;
+    // Count the tiles before any warp can see their flags, then take back the
+    // ones already flagged: `pending` never undercounts, even if a flagged
+    // tile's visit ends before this lane gets to its next instruction. The
+    // returned count is checked for wrap-around, which also makes the
+    // increment complete before the flags are set.
+    const uint32_t before = atomicAdd(p.pending, nc);
+    if (before + nc < before) {
+        raise_status(p.err, RT_ETIMEOUT);
+        return;
     }
+    uint32_t stale = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        if (c[k]) stale += mark_tile(p.flags, u[k], k == 0 ? self_bits : kHalo);
+    if (stale) atomicSub(p.pending, stale);
 }
 
 __device__ __forceinline__ const ReconImage &find_image(const SweepParams &p, int t)
