@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving leg at 800 tiles/s (0: skip)")
     ap.add_argument("--streams", type=int, default=3, help="streams the timed steps alternate between")
+    ap.add_argument("--no-configs", action="store_true", help="skip the configuration 1 and 3 legs")
     return ap.parse_args()
 
 
@@ -341,6 +342,61 @@ def run_native(a, rank, world, local_rank):
     for o_l, o_p, o_1 in zip(outs, outs_p, outs1):
         assert torch.equal(o_l["L"], o_p["L"]) and torch.equal(o_l["D"], o_1["D"])
 
+    # configuration 1: reconstruction only, one 512^2 image, median of 200
+    # timed runs after 20 warm-up runs, with the bytes the passes moved
+    config1 = None
+    config3 = None
+    if not a.no_configs and world == 1:
+        import synth
+        c1 = torch.from_numpy(synth.config1_image(1000)).to(dev)
+        r1 = torch.empty_like(c1)
+        for _ in range(20):
+            rt.reconstruct(c1, None, h_offset=30, out=r1, ctx=ctx, stream=stream)
+        t1 = []
+        for _ in range(200):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rt.reconstruct(c1, None, h_offset=30, out=r1, ctx=ctx, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            t1.append(e0.elapsed_time(e1))
+        v1, it1, _ = ctx.recon_stats()
+        config1 = {"image": "512x512, 60 disks, flat background", "median_ms": statistics.median(t1), "reps": 200,
+                   "warmup": 20, "tile_visits": v1, "tile_iterations": it1,
+                   "pass_bytes": it1 * PASSES_PER_ITERATION * TILE_PX * BYTES_PASS,
+                   "compulsory_bytes": BYTES_RECON * 512 * 512}
+        # configuration 3: 64 uneven tiles (sides 1024..4096 step 256, 50..400
+        # nuclei per Mpx) in one call captured in a CUDA graph, parameters
+        # from the autotuner; throughput in 4K-tile equivalents
+        from paper_1405_7958_gb300 import autotune
+        specs = synth.batch_sizes(64, 3000)
+        b3 = [rt.synth_tile(H, W, sd, ns, ctx=ctx) for H, W, ns, sd in specs]
+        px3 = sum(H * W for H, W, _, _ in specs)
+        tuned = autotune.tune(b3, reps=2, ctx=ctx, stream=stream)["best"]
+        p3 = rt.SegParams(variant=int(tuned["variant"]), max_local=int(tuned["max_local"]))
+        g3s = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(g3s):
+            o3 = rt.segment_batch(b3, p3, ctx=ctx, stream=g3s, want_recon=False, want_filled=False)
+        g3s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=g3s):
+            rt.segment_batch(b3, p3, outputs=o3, ctx=ctx, stream=g3s, want_recon=False, want_filled=False)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        t3 = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(g3s)
+            graph.replay()
+            e1.record(g3s)
+            e1.synchronize()
+            t3.append(e0.elapsed_time(e1))
+        ms3 = statistics.median(t3)
+        config3 = {"tiles": 64, "megapixels": px3 / 1e6, "tuned": tuned, "graph_replay_ms": ms3,
+                   "tile4k_equiv_s": px3 / 2 ** 24 / (ms3 / 1000.0), "tiles_s": 64 / (ms3 / 1000.0)}
+        del o3, b3, graph
+
     serving = None
     if a.serve_seconds > 0 and world == 1:
         from paper_1405_7958_gb300 import serve
@@ -453,6 +509,8 @@ def run_native(a, rank, world, local_rank):
             "plain_per_tile_tiles_s": world * per_tile_plain,
             "picker_choices": picks,
             "serving_batched_learned": serving,
+            "config1_recon_512": config1,
+            "config3_uneven_64_graph": config3,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

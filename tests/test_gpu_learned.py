@@ -208,3 +208,46 @@ def test_learned_policy_in_cuda_graph(rt):
             for k in ("R", "F", "L", "D"):
                 assert np.array_equal(host(o[k]), want[k])
     ctx.close()
+
+
+def test_trained_picker_gain_on_held_out_tiles(rt):
+    """What the trained network gains over the plain schedule: 16 held-out
+    uneven tiles (seeds outside the training and evaluation sets) run batched
+    with the trained picker and with the fixed plain schedule; the outputs are
+    identical and the times are compared (median of 5, CUDA events). On these
+    tiles the network picks the raster propagation, which the plain schedule
+    uses too, so the gain is about 1: the test bounds what the picker costs."""
+    import os
+    import statistics
+    from paper_1405_7958_gb300 import picker as pkmod
+    pk = pkmod.load(os.path.join(os.path.dirname(rt.__file__), "data", "picker_config4.npz"))
+    specs = synth.batch_sizes(16, 9100)
+    imgs = [rt.synth_tile(H, W, s, ns) for H, W, ns, s in specs]
+    ctx_l, ctx_p = rt.Context(), rt.Context()
+    pk.attach(ctx_l)
+    learned, plain = rt.SegParams(policy=1), rt.SegParams()
+    ol = rt.segment_batch(imgs, learned, ctx=ctx_l)
+    op = rt.segment_batch(imgs, plain, ctx=ctx_p)
+    torch.cuda.synchronize()
+    for a, b in zip(ol, op):
+        for k in ("R", "F", "L", "D"):
+            assert torch.equal(a[k], b[k])
+
+    def timed(params, ctx, outs):
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rt.segment_batch(imgs, params, outputs=outs, ctx=ctx)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    t_learned, t_plain = timed(learned, ctx_l, ol), timed(plain, ctx_p, op)
+    gain = t_plain / t_learned
+    print(f"trained picker: {t_learned:.2f} ms, plain: {t_plain:.2f} ms, gain {gain:.3f}, "
+          f"picks {rt.last_picks(ctx_l)}")
+    assert gain > 0.9
+    ctx_l.close()
+    ctx_p.close()
