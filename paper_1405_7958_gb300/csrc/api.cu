@@ -248,6 +248,7 @@ void carve_uf(Carve &cv, UfArgs &a, int H, int W)
     a.list = cv.take<int32_t>(N / 2 + 2);
     a.nlist = cv.take<uint32_t>(1);
     a.lroot = cv.take<uint16_t>(N);
+    a.bempty = cv.take<uint8_t>(nblk);
 }
 
 __global__ void copy_status_kernel(const int32_t *src, int32_t *dst)

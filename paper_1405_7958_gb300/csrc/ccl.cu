@@ -31,7 +31,7 @@ size_t uf_workspace_bytes(int H, int W)
     const size_t N = (size_t)H * W;
     const size_t nblk = (size_t)ceil_div(W, kB) * ceil_div(H, kB);
     return 2 * N * sizeof(int32_t) + nblk * kUfEdge * sizeof(int32_t) + (N / 2 + 2) * sizeof(int32_t) +
-           N * sizeof(uint16_t) + 8 * 256;
+           N * sizeof(uint16_t) + nblk + 8 * 256;
 }
 
 __device__ __forceinline__ bool is_fg(const uint8_t *in, int64_t ld, int r, int c, int source)
@@ -128,7 +128,7 @@ __device__ __forceinline__ void union_g(int32_t *U, int32_t a, int32_t b)
 // starts at its upper-right neighbour. On return roots[k] holds the local
 // index (lr * 32 + c) of the root of the thread's k-th pixel, or -1.
 template <int CONN>
-__device__ __forceinline__ void local_labels(const UfArgs &a, int source, int *P, uint32_t *M,
+__device__ __forceinline__ bool local_labels(const UfArgs &a, int source, int *P, uint32_t *M,
                                              int roots[kRowsPerThread])
 {
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -152,7 +152,7 @@ __device__ __forceinline__ void local_labels(const UfArgs &a, int source, int *P
     if (!__syncthreads_or(any != 0)) {
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) roots[k] = -1;
-        return;
+        return false;
     }
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
@@ -183,6 +183,7 @@ __device__ __forceinline__ void local_labels(const UfArgs &a, int source, int *P
         const int i = (w * kRowsPerThread + k) * kB + tx;
         roots[k] = P[i] >= 0 ? find_s_halve(P, i) : -1;
     }
+    return true;
 }
 
 __device__ __forceinline__ int32_t global_index(const UfArgs &a, int local)
@@ -199,10 +200,20 @@ __global__ void __launch_bounds__(kThreads) uf_local_kernel(UfArgs a, int source
     __shared__ int cnt[kB * kB];
     __shared__ uint32_t M[kB];
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kB * kB; i += blockDim.x) cnt[i] = 0;
     int roots[kRowsPerThread];
-    local_labels<CONN>(a, source, P, M, roots);
+    const bool nonempty = local_labels<CONN>(a, source, P, M, roots);
     const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
+    const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    int32_t *edge = a.edge + blk * kUfEdge;
+    if (!nonempty) {   // no roots, no edge roots; the output pass skips the block
+        if (threadIdx.x < kUfEdge) edge[threadIdx.x] = -1;
+        if (threadIdx.x == 0) a.bempty[blk] = 1;
+        return;
+    }
+    if (threadIdx.x == 0) a.bempty[blk] = 0;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) cnt[(w * kRowsPerThread + k) * kB + tx] = 0;
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         if (roots[k] < 0) continue;
@@ -217,7 +228,6 @@ __global__ void __launch_bounds__(kThreads) uf_local_kernel(UfArgs a, int source
         const int r = r0 + w * kRowsPerThread + k, c = c0 + tx;
         if (r < a.H && c < a.W) a.lroot[(int64_t)r * a.W + c] = roots[k] >= 0 ? (uint16_t)roots[k] : (uint16_t)0xFFFFu;
     }
-    int32_t *edge = a.edge + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kUfEdge;
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int lr = w * kRowsPerThread + k;
@@ -331,11 +341,12 @@ __global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfArgs a, int32_t *
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB, c = c0 + tx;
     const int64_t wpr = ceil_div(a.W, 32);
+    const bool empty = a.bempty[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] != 0;
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int r = r0 + w * kRowsPerThread + k;
         const bool in = r < a.H && c < a.W;
-        const uint32_t lr = in ? a.lroot[(int64_t)r * a.W + c] : 0xFFFFu;
+        const uint32_t lr = in && !empty ? a.lroot[(int64_t)r * a.W + c] : 0xFFFFu;
         int32_t out = -1;
         if (lr != 0xFFFFu) {
             const int32_t root = a.U[global_index(a, (int)lr)];

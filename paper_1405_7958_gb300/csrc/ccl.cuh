@@ -22,7 +22,9 @@ struct UfArgs {
                          // left column, right column pixels (-1 = not in a component)
     int32_t *list;       // the local roots
     uint32_t *nlist;     // their number
-    uint16_t *lroot;     // per pixel (stride W): its local root inside its block (lr * 32 + lc), 0xFFFF = none
+    uint16_t *lroot;     // per pixel (stride W): its local root inside its block (lr * 32 + lc), 0xFFFF = none;
+                         // not written for blocks without foreground
+    uint8_t *bempty;     // per block: 1 = no foreground
 };
 
 // Workspace bytes the arrays need for an H x W image.
