@@ -378,23 +378,28 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
         {
             uint32_t *row = wb.sRT + lane * kTS;
             const uint32_t *irow = wb.sIT + lane * kTS;
-            uint32_t x = wb.sHL[lane + 1], hd = 0;
+            // x2 holds the incoming value in both halves. Left to right:
+            // t's low half is the new left pixel a (t's high half is not
+            // used); with a in both halves the same clamp gives the new word
+            // (its low half stays a, because a already absorbed w_lo and is
+            // at most i_lo). Right to left mirrors it.
+            uint32_t x2 = __byte_perm(wb.sHL[lane + 1], 0u, 0x1010), hd = 0;
 #pragma unroll 8
             for (int j = 0; j < kTW / 2; ++j) {
                 const uint32_t w = row[j], iw = irow[j];
-                const uint32_t a = min(max(w & 0xffffu, x), iw & 0xffffu);
-                x = min(max(w >> 16, a), iw >> 16);
-                const uint32_t nw = a | (x << 16);
+                const uint32_t t = vmin2(vmax2(w, x2), iw);
+                const uint32_t nw = vmin2(vmax2(w, __byte_perm(t, 0u, 0x1010)), iw);
+                x2 = __byte_perm(nw, 0u, 0x3232);
                 row[j] = nw;
                 hd |= nw ^ w;
             }
-            x = wb.sHR[lane + 1];
+            x2 = __byte_perm(wb.sHR[lane + 1], 0u, 0x1010);
 #pragma unroll 8
             for (int j = kTW / 2 - 1; j >= 0; --j) {
                 const uint32_t w = row[j], iw = irow[j];
-                const uint32_t b = min(max(w >> 16, x), iw >> 16);
-                x = min(max(w & 0xffffu, b), iw & 0xffffu);
-                const uint32_t nw = x | (b << 16);
+                const uint32_t t = vmin2(vmax2(w, x2), iw);
+                const uint32_t nw = vmin2(vmax2(w, __byte_perm(t, 0u, 0x3232)), iw);
+                x2 = __byte_perm(nw, 0u, 0x1010);
                 row[j] = nw;
                 hd |= nw ^ w;
             }
