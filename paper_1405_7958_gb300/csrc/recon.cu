@@ -325,14 +325,11 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
         for (int r = 0; r < kTH; ++r) {
             uint32_t m = vmax2(R[r], prev);
             if (CONN == 8) {
-                uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
-                uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
-                // volatile: the loads stay in the loop (hoisted, 64 halo words
-                // would not fit in the registers)
-                const uint32_t hl = reinterpret_cast<volatile const uint32_t *>(wb.sHL)[r];
-                const uint32_t hr = reinterpret_cast<volatile const uint32_t *>(wb.sHR)[r];
-                sl = lane == 0 ? hl << 16 : sl;
-                sr = lane == 31 ? hr : sr;
+                // lanes 0 and 31 get their own word back from the shuffles:
+                // the extra terms are in-tile neighbours anyway; the halo
+                // columns enter through the row pass
+                const uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
+                const uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
                 m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
             }
             const uint32_t nv = vmin2(m, Is[r * kTS]);
@@ -352,12 +349,8 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
         for (int r = kTH - 1; r >= 0; --r) {
             uint32_t m = vmax2(R[r], prev);
             if (CONN == 8) {
-                uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
-                uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
-                const uint32_t hl = reinterpret_cast<volatile const uint32_t *>(wb.sHL)[r + 2];
-                const uint32_t hr = reinterpret_cast<volatile const uint32_t *>(wb.sHR)[r + 2];
-                sl = lane == 0 ? hl << 16 : sl;
-                sr = lane == 31 ? hr : sr;
+                const uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
+                const uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
                 m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
             }
             const uint32_t nv = vmin2(m, Is[r * kTS]);
@@ -383,7 +376,14 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
             // used); with a in both halves the same clamp gives the new word
             // (its low half stays a, because a already absorbed w_lo and is
             // at most i_lo). Right to left mirrors it.
-            uint32_t x2 = __byte_perm(wb.sHL[lane + 1], 0u, 0x1010), hd = 0;
+            // the halo pixels next to the row's ends: the same row's, and for
+            // 8-connectivity also the rows above and below it
+            uint32_t hl = wb.sHL[lane + 1], hr = wb.sHR[lane + 1];
+            if (CONN == 8) {
+                hl = max(hl, max(wb.sHL[lane], wb.sHL[lane + 2]));
+                hr = max(hr, max(wb.sHR[lane], wb.sHR[lane + 2]));
+            }
+            uint32_t x2 = __byte_perm(hl, 0u, 0x1010), hd = 0;
 #pragma unroll 8
             for (int j = 0; j < kTW / 2; ++j) {
                 const uint32_t w = row[j], iw = irow[j];
@@ -393,7 +393,7 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
                 row[j] = nw;
                 hd |= nw ^ w;
             }
-            x2 = __byte_perm(wb.sHR[lane + 1], 0u, 0x1010);
+            x2 = __byte_perm(hr, 0u, 0x1010);
 #pragma unroll 8
             for (int j = kTW / 2 - 1; j >= 0; --j) {
                 const uint32_t w = row[j], iw = irow[j];
