@@ -521,6 +521,7 @@ rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int
     a.d2 = d2;
     a.ld_d2 = ld_d2;
     a.g = cv.take<uint16_t>((size_t)H * W);
+    a.cmask = nullptr;
     a.seg = cv.take<int32_t>((size_t)2 * ceil_div(H, 32) * W);
     a.any_bg = cv.take<uint32_t>(1);
     if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
@@ -834,7 +835,8 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
             ea.ld_d2 = t.ld_d2;
             Carve ec;
             ec.base = edt_ws;
-            ea.g = ec.take<uint16_t>((size_t)H * W);
+            ea.g = nullptr;   // the bit-plane path computes g while staging each row
+            ea.cmask = ec.take<uint32_t>((size_t)ceil_div(H, 32) * W);
             ea.seg = ec.take<int32_t>((size_t)2 * ceil_div(H, 32) * W);
             ea.any_bg = ec.take<uint32_t>(1);
             {

@@ -8,6 +8,11 @@
 // Vertical pass: columns are cut into 32-row segments; a first kernel
 // records each segment's first and last background row, a second one walks
 // every segment with the carries from the segments above and below.
+// With a bit-plane input g is never stored: a first kernel turns each 32 x 32
+// block's row words into column masks (ballots), a second records for every
+// segment and column the nearest background row above and below the
+// segment, and the horizontal pass computes the g values of its row from
+// those (bit scans of the column's mask) while staging them.
 // Horizontal pass: a CTA per row stages g in shared memory. For pixel c the
 // candidate c' = c gives g(r,c)^2, and any c' with |c - c'| >= sqrt(best)
 // cannot win, so the search runs outward from c and stops as soon as
@@ -24,7 +29,7 @@ constexpr uint16_t kInf = 0xFFFFu;
 size_t edt_workspace_bytes(int H, int W)
 {
     const int64_t nseg = ceil_div(H, kSeg);
-    return (size_t)H * W * sizeof(uint16_t) + (size_t)2 * nseg * W * sizeof(int32_t) + 256;
+    return (size_t)H * W * sizeof(uint16_t) + (size_t)3 * nseg * W * sizeof(int32_t) + 512;
 }
 
 __device__ __forceinline__ bool edt_is_bg(const EdtArgs &a, int r, int c)
@@ -88,6 +93,93 @@ __global__ void edt_col_kernel(EdtArgs a)
     }
 }
 
+// Bit-plane input: a warp covers the 32 columns of one plane word and one
+// segment. Lane i loads the word of row rb + i; 32 ballots turn the rows'
+// words into the columns' masks, lane j getting column 32 * wc + j with bit
+// i set where row rb + i is background. Rows past the end count as
+// foreground.
+__device__ __forceinline__ uint32_t seg_bg_mask(const EdtArgs &a, int64_t wpr, int wc, int rb, int lane)
+{
+    const int r = rb + lane;
+    const uint32_t w = r < a.H ? __ldg(a.bits + (int64_t)r * wpr + wc) : 0xffffffffu;
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t b = __ballot_sync(0xffffffffu, !((w >> j) & 1u));
+        m = lane == j ? b : m;
+    }
+    return m;
+}
+
+// warp per (plane word column, segment): the segment's column masks
+__global__ void __launch_bounds__(128) edt_mask_bits_kernel(EdtArgs a)
+{
+    const int64_t wpr = ceil_div(a.W, 32);
+    const int wc = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (wc >= wpr) return;
+    const int s = blockIdx.y, rb = s * kSeg;
+    const uint32_t bg = seg_bg_mask(a, wpr, wc, rb, lane);
+    const int c = wc * 32 + lane;
+    if (c >= a.W) return;
+    a.cmask[(int64_t)s * a.W + c] = bg;
+    if (bg && *a.any_bg == 0) atomicOr(a.any_bg, 1u);
+}
+
+// thread per (column, segment): the last background row above the segment
+// and the first one below it (-1: none)
+__global__ void edt_chase_bits_kernel(EdtArgs a)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (c >= a.W) return;
+    const int nseg = (int)ceil_div(a.H, kSeg);
+    int above = -1;
+    for (int t = s - 1; t >= 0; --t) {
+        const uint32_t m = a.cmask[(int64_t)t * a.W + c];
+        if (m) { above = t * kSeg + 31 - __clz(m); break; }
+    }
+    int below = -1;
+    for (int t = s + 1; t < nseg; ++t) {
+        const uint32_t m = a.cmask[(int64_t)t * a.W + c];
+        if (m) { below = t * kSeg + __ffs(m) - 1; break; }
+    }
+    a.seg[(int64_t)s * a.W + c] = above;
+    a.seg[(int64_t)(nseg + s) * a.W + c] = below;
+}
+
+// d2 of one row from its g values in shared memory: for pixel c the search
+// runs outward from c and stops once (c - c')^2 reaches the best value
+__device__ __forceinline__ void edt_row_search(const uint16_t *sg, int W, bool any, int32_t *out)
+{
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        if (!any) {
+            out[c] = -1;
+            continue;
+        }
+        const int gc = sg[c];
+        long long best = gc == kInf ? 0x7fffffffffffLL : (long long)gc * gc;
+        for (int d = 1; (long long)d * d < best; ++d) {
+            const int cl = c - d, cr = c + d;
+            if (cl < 0 && cr >= W) break;
+            if (cl >= 0) {
+                const int g = sg[cl];
+                if (g != kInf) {
+                    const long long v = (long long)d * d + (long long)g * g;
+                    if (v < best) best = v;
+                }
+            }
+            if (cr < W) {
+                const int g = sg[cr];
+                if (g != kInf) {
+                    const long long v = (long long)d * d + (long long)g * g;
+                    if (v < best) best = v;
+                }
+            }
+        }
+        out[c] = (int32_t)best;
+    }
+}
+
 // CTA per row: exact minimum over columns with early termination
 __global__ void edt_row_kernel(EdtArgs a)
 {
@@ -102,35 +194,35 @@ __global__ void edt_row_kernel(EdtArgs a)
         for (int c = threadIdx.x; c < a.W; c += blockDim.x) sg[c] = grow[c];
     }
     __syncthreads();
-    const bool any = *a.any_bg != 0;
-    int32_t *out = a.d2 + (int64_t)r * a.ld_d2;
+    edt_row_search(sg, a.W, *a.any_bg != 0, a.d2 + (int64_t)r * a.ld_d2);
+}
+
+// CTA per row, bit-plane input: g of the row from the column masks of its
+// segment (and, where the segment has no background on one side of the row,
+// the nearest background beyond it), then the same search
+__global__ void edt_row_bits_kernel(EdtArgs a)
+{
+    extern __shared__ uint16_t sg[];
+    const int r = blockIdx.x, s = r / kSeg, i = r % kSeg, rb = s * kSeg;
+    const int nseg = (int)ceil_div(a.H, kSeg);
+    const uint32_t *cm = a.cmask + (int64_t)s * a.W;
     for (int c = threadIdx.x; c < a.W; c += blockDim.x) {
-        if (!any) {
-            out[c] = -1;
-            continue;
+        const uint32_t m = cm[c];
+        uint16_t g = 0;
+        if (!((m >> i) & 1u)) {
+            const uint32_t upto = m & (0xffffffffu >> (31 - i));   // rows rb .. r
+            const uint32_t from = m & (0xffffffffu << i);          // rows r .. rb + 31
+            const int up = upto ? rb + 31 - __clz(upto) : a.seg[(int64_t)s * a.W + c];
+            const int dn = from ? rb + __ffs(from) - 1 : a.seg[(int64_t)(nseg + s) * a.W + c];
+            int d = 0x7fffffff;
+            if (up >= 0) d = r - up;
+            if (dn >= 0 && dn - r < d) d = dn - r;
+            g = d == 0x7fffffff ? kInf : (uint16_t)d;
         }
-        const int gc = sg[c];
-        long long best = gc == kInf ? 0x7fffffffffffLL : (long long)gc * gc;
-        for (int d = 1; (long long)d * d < best; ++d) {
-            const int cl = c - d, cr = c + d;
-            if (cl < 0 && cr >= a.W) break;
-            if (cl >= 0) {
-                const int g = sg[cl];
-                if (g != kInf) {
-                    const long long v = (long long)d * d + (long long)g * g;
-                    if (v < best) best = v;
-                }
-            }
-            if (cr < a.W) {
-                const int g = sg[cr];
-                if (g != kInf) {
-                    const long long v = (long long)d * d + (long long)g * g;
-                    if (v < best) best = v;
-                }
-            }
-        }
-        out[c] = (int32_t)best;
+        sg[c] = g;
     }
+    __syncthreads();
+    edt_row_search(sg, a.W, *a.any_bg != 0, a.d2 + (int64_t)r * a.ld_d2);
 }
 
 cudaError_t launch_edt(const EdtArgs &a, cudaStream_t s)
@@ -138,17 +230,26 @@ cudaError_t launch_edt(const EdtArgs &a, cudaStream_t s)
     const int nseg = (int)ceil_div(a.H, kSeg);
     cudaError_t e = cudaMemsetAsync(a.any_bg, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const dim3 g1((unsigned)ceil_div(a.W, 128), (unsigned)nseg);
-    edt_seg_kernel<<<g1, 128, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    edt_col_kernel<<<g1, 128, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = (size_t)a.W * sizeof(uint16_t);
+    const void *row_fn = a.bits ? (const void *)edt_row_bits_kernel : (const void *)edt_row_kernel;
     if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(edt_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(row_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    edt_row_kernel<<<(unsigned)a.H, 256, smem, s>>>(a);
+    if (a.bits) {
+        edt_mask_bits_kernel<<<dim3((unsigned)ceil_div(ceil_div(a.W, 32), 4), (unsigned)nseg), 128, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        edt_chase_bits_kernel<<<dim3((unsigned)ceil_div(a.W, 128), (unsigned)nseg), 128, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        edt_row_bits_kernel<<<(unsigned)a.H, 256, smem, s>>>(a);
+    } else {
+        const dim3 g1((unsigned)ceil_div(a.W, 128), (unsigned)nseg);
+        edt_seg_kernel<<<g1, 128, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        edt_col_kernel<<<g1, 128, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        edt_row_kernel<<<(unsigned)a.H, 256, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

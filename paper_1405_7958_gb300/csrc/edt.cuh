@@ -15,7 +15,9 @@ struct EdtArgs {
     int H, W;
     int32_t *d2;            // output
     int64_t ld_d2;
-    uint16_t *g;            // workspace: vertical distance, H x W (stride W)
+    uint16_t *g;            // workspace (byte / label input): vertical distance, H x W (stride W)
+    uint32_t *cmask;        // workspace (bit-plane input): per segment s and column c, bit i set
+                            // where row 32 s + i is background (nseg x W)
     int32_t *seg;           // workspace: 2 x nseg x W (first / last background row per segment)
     uint32_t *any_bg;       // workspace word
 };
