@@ -206,20 +206,32 @@ __global__ void edt_row_bits_kernel(EdtArgs a)
     const int r = blockIdx.x, s = r / kSeg, i = r % kSeg, rb = s * kSeg;
     const int nseg = (int)ceil_div(a.H, kSeg);
     const uint32_t *cm = a.cmask + (int64_t)s * a.W;
-    for (int c = threadIdx.x; c < a.W; c += blockDim.x) {
-        const uint32_t m = cm[c];
-        uint16_t g = 0;
-        if (!((m >> i) & 1u)) {
-            const uint32_t upto = m & (0xffffffffu >> (31 - i));   // rows rb .. r
-            const uint32_t from = m & (0xffffffffu << i);          // rows r .. rb + 31
-            const int up = upto ? rb + 31 - __clz(upto) : a.seg[(int64_t)s * a.W + c];
-            const int dn = from ? rb + __ffs(from) - 1 : a.seg[(int64_t)(nseg + s) * a.W + c];
-            int d = 0x7fffffff;
-            if (up >= 0) d = r - up;
-            if (dn >= 0 && dn - r < d) d = dn - r;
-            g = d == 0x7fffffff ? kInf : (uint16_t)d;
+    // four columns per thread at a time: their mask loads are issued together
+    for (int c0 = threadIdx.x; c0 < a.W; c0 += 4 * blockDim.x) {
+        uint32_t mm[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * blockDim.x;
+            mm[u] = c < a.W ? __ldg(cm + c) : 0xffffffffu;
         }
-        sg[c] = g;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * blockDim.x;
+            if (c >= a.W) break;
+            const uint32_t m = mm[u];
+            uint16_t g = 0;
+            if (!((m >> i) & 1u)) {
+                const uint32_t upto = m & (0xffffffffu >> (31 - i));   // rows rb .. r
+                const uint32_t from = m & (0xffffffffu << i);          // rows r .. rb + 31
+                const int up = upto ? rb + 31 - __clz(upto) : a.seg[(int64_t)s * a.W + c];
+                const int dn = from ? rb + __ffs(from) - 1 : a.seg[(int64_t)(nseg + s) * a.W + c];
+                int d = 0x7fffffff;
+                if (up >= 0) d = r - up;
+                if (dn >= 0 && dn - r < d) d = dn - r;
+                g = d == 0x7fffffff ? kInf : (uint16_t)d;
+            }
+            sg[c] = g;
+        }
     }
     __syncthreads();
     edt_row_search(sg, a.W, *a.any_bg != 0, a.d2 + (int64_t)r * a.ld_d2);
