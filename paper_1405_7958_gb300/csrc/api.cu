@@ -589,7 +589,7 @@ rt_status rt_tile_features(rt_ctx *ctx, const uint8_t *const *imgs, const int64_
     cv = Carve();
     cv.base = (char *)ctx->ws;
     layout(cv, fb);
-    ctx->launches += 3;
+    ctx->launches += 4;
     return cuda_status(launch_features(fb, out, s));
 }
 
@@ -767,7 +767,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
                 RT_CUDA_TRY(launch_features(fb, feat, s));
                 RT_CUDA_TRY(launch_mlp_forward(ctx->picker_wb, ctx->picker_norm, feat, cn, nullptr, nullptr,
                                                picks_dev, s));
-                ctx->launches += 4;
+                ctx->launches += 5;
             }
             st = run_recon(ctx, b, w, P.conn_recon, P.variant, P.max_local, w.err, s, picks_dev);
             if (st != RT_OK) return st;

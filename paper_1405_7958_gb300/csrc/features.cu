@@ -18,9 +18,13 @@
 
 namespace rtk {
 
-// pass 1, CTA = 64 rows x 256 columns, thread = column: histogram (per warp
-// in shared memory, then global), and per 8 x 8 block the dark count and the
-// maximum (reduced over the 8 lanes of a block column)
+// pass 1, CTA = 64 rows x 1024 columns, thread = 4 adjacent columns (one
+// 32-bit load per row where the row start allows it): histogram (per warp in
+// shared memory, then global), and per 8 x 8 block the dark count and the
+// maximum (a block's two threads are neighbouring lanes)
+constexpr int kFeatCols = 4;
+constexpr int kFeatSpan = 256 * kFeatCols;
+
 __global__ void __launch_bounds__(256) feat_block_kernel(FeatBatch fb)
 {
     // one 256-bin histogram per warp (values of neighbouring pixels cluster,
@@ -31,30 +35,36 @@ __global__ void __launch_bounds__(256) feat_block_kernel(FeatBatch fb)
 #pragma unroll
     for (int k = 0; k < 8; ++k) sh[k][threadIdx.x] = 0;
     __syncthreads();
-    const int c = blockIdx.x * 256 + threadIdx.x;
+    const int c0 = blockIdx.x * kFeatSpan + threadIdx.x * kFeatCols;
     const int r0 = blockIdx.y * 64;
-    if (r0 < d.H && blockIdx.x * 256 < d.W) {
+    if (r0 < d.H && blockIdx.x * kFeatSpan < d.W) {
         const int bw = (d.W + 7) / 8;
+        const int nc = max(0, min(kFeatCols, d.W - c0));   // this thread's columns inside the image
+        const bool word = nc == kFeatCols && ((((uintptr_t)d.img) | (uintptr_t)d.ld) & 3u) == 0;
         for (int g = 0; g < 8; ++g) {
             const int rb = r0 + 8 * g;
             if (rb >= d.H) break;
             int dark = 0, mx = 0;
-            if (c < d.W) {
-                const int re = min(d.H, rb + 8);
-                for (int r = rb; r < re; ++r) {
-                    const int v = d.img[(int64_t)r * d.ld + c];
+            const int re = min(d.H, rb + 8);
+            for (int r = rb; r < re; ++r) {
+                const uint8_t *row = d.img + (int64_t)r * d.ld + c0;
+                uint32_t v4 = 0;
+                if (word) {
+                    v4 = *reinterpret_cast<const uint32_t *>(row);
+                } else {
+                    for (int k = 0; k < nc; ++k) v4 |= (uint32_t)row[k] << (8 * k);
+                }
+                for (int k = 0; k < nc; ++k) {
+                    const int v = (v4 >> (8 * k)) & 0xff;
                     atomicAdd(&sh[warp][v], 1u);
                     dark += v < 80;
                     mx = max(mx, v);
                 }
             }
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-                dark += __shfl_xor_sync(0xffffffffu, dark, o);
-                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            }
-            if ((threadIdx.x & 7) == 0 && c < d.W) {
-                const int b = (rb / 8) * bw + c / 8;
+            dark += __shfl_xor_sync(0xffffffffu, dark, 1);
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            if ((threadIdx.x & 1) == 0 && c0 < d.W) {
+                const int b = (rb / 8) * bw + c0 / 8;
                 d.dark[b] = (uint8_t)dark;
                 d.bmax[b] = (uint8_t)mx;
             }
@@ -65,6 +75,14 @@ __global__ void __launch_bounds__(256) feat_block_kernel(FeatBatch fb)
 #pragma unroll
     for (int k = 0; k < 8; ++k) tot += sh[k][threadIdx.x];
     if (tot) atomicAdd(d.hist + threadIdx.x, tot);
+}
+
+// clears the per-image accumulators of a call (one launch for the batch)
+__global__ void feat_zero_kernel(FeatBatch fb)
+{
+    const FeatImage &d = fb.img[blockIdx.x];
+    d.hist[threadIdx.x] = 0;
+    if (threadIdx.x < 4) d.acc[threadIdx.x] = 0;
 }
 
 __device__ __forceinline__ int marker_of(const uint8_t *D, int bh, int bw, int r, int c)
@@ -219,13 +237,13 @@ cudaError_t launch_features(const FeatBatch &fb, float *out, cudaStream_t s)
         maxW = d.W > maxW ? d.W : maxW;
         const int nb = ((d.H + 7) / 8) * ((d.W + 7) / 8);
         maxnb = nb > maxnb ? nb : maxnb;
-        cudaError_t e = cudaMemsetAsync(d.hist, 0, 256 * sizeof(uint32_t), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d.acc, 0, 4 * sizeof(unsigned long long), s);
-        if (e != cudaSuccess) return e;
     }
-    feat_block_kernel<<<dim3((unsigned)ceil_div(maxW, 256), (unsigned)ceil_div(maxH, 64), (unsigned)fb.n), 256, 0, s>>>(fb);
+    feat_zero_kernel<<<(unsigned)fb.n, 256, 0, s>>>(fb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    feat_block_kernel<<<dim3((unsigned)ceil_div(maxW, kFeatSpan), (unsigned)ceil_div(maxH, 64), (unsigned)fb.n), 256, 0,
+                        s>>>(fb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int gx = (int)ceil_div(maxnb, 256);
     if (gx > 512) gx = 512;
     feat_count_kernel<<<dim3((unsigned)gx, (unsigned)fb.n), 256, 0, s>>>(fb);
