@@ -251,9 +251,10 @@ void carve_uf(Carve &cv, UfArgs &a, int H, int W)
     a.bempty = cv.take<uint8_t>(nblk);
 }
 
+// a tile's status word: the device status of the chunk that carried it
 __global__ void copy_status_kernel(const int32_t *src, int32_t *dst)
 {
-    if (threadIdx.x == 0 && *src != 0) atomicCAS(dst, 0, *src);
+    if (threadIdx.x == 0) *dst = *src;
 }
 
 }  // namespace
@@ -845,7 +846,6 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
                 RT_CUDA_TRY(launch_edt(ea, s));
             }
             if (t.status) {
-                RT_CUDA_TRY(cudaMemsetAsync(t.status, 0, sizeof(int32_t), s));
                 copy_status_kernel<<<1, 32, 0, s>>>(w.err, t.status);
                 ctx->launches += 1;
                 RT_CUDA_TRY(cudaGetLastError());
