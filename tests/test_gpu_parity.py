@@ -196,6 +196,35 @@ def test_chain_small(rt):
     check_chain(rt.segment_batch([dev(I)])[0], I)
 
 
+def test_chain_edt_bit_plane_edge_cases(rt):
+    """The chain's distance transform runs on the kept-pixel bit plane. Its
+    degenerate inputs: every pixel kept (no background anywhere: -1), a kept
+    band across the whole width (for rows inside it the nearest background
+    lies several 32-row segments away, above and below), a tall kept bar,
+    and nothing kept (0 everywhere); ragged sizes throughout."""
+    band = np.full((300, 120), 200, np.uint8)
+    band[40:251, :] = 40
+    bar = np.full((300, 200), 200, np.uint8)
+    bar[10:291, 50:61] = 40
+    cases = [np.full((77, 101), 40, np.uint8), band, bar, np.full((45, 70), 200, np.uint8)]
+    p = rt.SegParams(max_area=10 ** 9)
+    got = []
+    for I in cases:
+        out = rt.segment_batch([dev(I)], p)[0]
+        want = oracle.chain(I, max_area=10 ** 9)
+        for k in ("R", "F", "L", "D"):
+            assert np.array_equal(host(out[k]), want[k]), (I.shape, k)
+        assert int(out["n_kept"].item()) == want["n_kept"]
+        assert int(out["status"].item()) == 0
+        got.append(host(out["D"]))
+    # closed forms
+    assert (got[0] == -1).all()
+    r = np.arange(300)[:, None]
+    inside = (r >= 40) & (r <= 250)
+    assert np.array_equal(got[1], np.broadcast_to(np.where(inside, np.minimum(r - 39, 251 - r) ** 2, 0), (300, 120)))
+    assert (got[3] == 0).all()
+
+
 def test_chain_batch_uneven(rt):
     shapes = [(300, 700), (1024, 256), (129, 131)]
     imgs = [synth.config2_tile(100 + i, H=H, W=W) for i, (H, W) in enumerate(shapes)]
