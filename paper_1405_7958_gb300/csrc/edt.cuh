@@ -18,7 +18,9 @@ struct EdtArgs {
     uint16_t *g;            // workspace (byte / label input): vertical distance, H x W (stride W)
     uint32_t *cmask;        // workspace (bit-plane input): per segment s and column c, bit i set
                             // where row 32 s + i is background (nseg x W)
-    int32_t *seg;           // workspace: 2 x nseg x W (first / last background row per segment)
+    int32_t *seg;           // workspace: 2 x nseg x W; byte / label input: first / last background
+                            // row of each segment; bit-plane input: last background row above and
+                            // first below each segment (-1: none)
     uint32_t *any_bg;       // workspace word
 };
 
