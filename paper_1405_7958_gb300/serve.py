@@ -111,6 +111,21 @@ def _release(r, hp: PinnedPool, keep: bool):
         r.out_L = r.out_D = None
 
 
+def admit(pending: list, in_use: int, budget_bytes: int, max_batch: int):
+    """Takes requests from the front of `pending` (arrival order) while their
+    device bytes fit the budget beside the bytes in use, at most max_batch; a
+    request larger than the whole budget is taken alone once nothing else is
+    in use. Returns (taken requests, bytes in use)."""
+    take = []
+    while pending and len(take) < max_batch:
+        need = pending[0].H * pending[0].W * BYTES_PER_PX
+        if in_use + need > budget_bytes and (take or in_use > 0):
+            break
+        in_use += need
+        take.append(pending.pop(0))
+    return take, in_use
+
+
 def run_plain(reqs, pool, variant=rt.RT_RASTER, ctx=None, keep: bool = False):
     """One tile at a time, fixed variant, one stream."""
     ctx = ctx or rt.Context()
@@ -163,14 +178,7 @@ def run_batched(reqs, pool, budget_bytes: int = 40 << 30, max_batch: int = 32, n
         # admit and launch on a free stream
         free = [k for k, b in enumerate(busy) if b is None]
         if pending and free:
-            take = []
-            while pending and len(take) < max_batch:
-                need = pending[0].H * pending[0].W * BYTES_PER_PX
-                if in_use + need > budget_bytes and (take or in_use > 0):
-                    break
-                r = pending.pop(0)
-                in_use += need
-                take.append(r)
+            take, in_use = admit(pending, in_use, budget_bytes, max_batch)
             if take:
                 k = free[0]
                 s = streams[k]
