@@ -176,6 +176,29 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- CPU oracle
+def cpu_model() -> str:
+    """The host CPU's model name (from lscpu or /proc/cpuinfo; Arm cores
+    report their implementer / part numbers instead of a name)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:   # a missing tool or odd output only loses the name
+        pass
+    try:
+        with open("/proc/cpuinfo", errors="replace") as fh:
+            info = fh.read()
+        for key in ("model name", "CPU part"):
+            for line in info.splitlines():
+                if line.lower().startswith(key.lower()):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def oracle_tiles_per_s(tiles, threads):
     """Oracle chain over `tiles`, one tile per host thread (the C oracle
     releases the GIL). Returns (tiles/s, seconds)."""
@@ -210,7 +233,7 @@ def run_reference(a, rank, world):
         "data": "synthetic",
         "config": {"workload": f"segmentation chain, {a.batch} x {a.size}x{a.size} nuclei tiles per step",
                    "tiles_per_step": a.batch, "side": a.size},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
                          "sample": f"{a.batch} tiles of {a.size}x{a.size} per step, one tile per host thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -498,7 +521,7 @@ def run_native(a, rank, world, local_rank):
     if rank == 0 and not a.no_cpu:
         threads = min(os.cpu_count() or 1, a.batch)
         v, dt = oracle_tiles_per_s(tiles, threads)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"the {a.batch} bench tiles ({a.size}x{a.size}), one per host thread, {dt:.1f} s"}
 
     if world > 1:
