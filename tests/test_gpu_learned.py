@@ -47,8 +47,11 @@ def test_gpu_generator_4k_tile(rt):
 
 
 def test_features_match_oracle(rt):
+    from test_oracle_learned import _frontier_image
+    from golden.load import load
     imgs = [synth.config2_tile(5, H=333, W=517), synth.config1_image(1000), synth.random_binary(64, 40, 2, 500) * 200,
-            np.full((9, 13), 77, np.uint8), synth.config2_tile(9, H=1024, W=2048)]
+            np.full((9, 13), 77, np.uint8), synth.config2_tile(9, H=1024, W=2048),
+            _frontier_image(load("features_frontier.txt")["D"])]
     got = host(rt.tile_features([torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in imgs]))
     for g, x in zip(got, imgs):
         want = OF.features(x)

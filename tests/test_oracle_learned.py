@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 from scipy import stats
 
+from golden.load import load
 from oracle import features as F
 from oracle import mlp as M
 
@@ -84,3 +85,42 @@ def test_adamw_first_step_closed_form():
     new, m, v = M.adamw(master, grad, np.zeros(2), np.zeros(2), 1, lr=0.1, wd=0.0, eps=0.0)
     # first bias-corrected step moves every parameter by lr * sign(grad)
     assert np.allclose(new, master - 0.1 * np.sign(grad))
+
+
+def _frontier_image(D):
+    """48 x 48 image whose 8 x 8 block maxima are D: the block's maximum sits
+    at a position that varies from block to block, the rest holds D // 2."""
+    bh, bw = D.shape
+    I = np.zeros((8 * bh, 8 * bw), np.uint8)
+    for r in range(bh):
+        for c in range(bw):
+            I[8 * r:8 * r + 8, 8 * c:8 * c + 8] = D[r, c] // 2
+            I[8 * r + (r + c) % 8, 8 * c + (2 * r + c) % 8] = D[r, c]
+    return I
+
+
+def _count_with(D, offsets):
+    """The frontier count of the fixture's rule with another neighbour set
+    (written out here, not taken from the oracle)."""
+    Jd = np.maximum(D - 30, 0)
+    Jd[0, :], Jd[-1, :], Jd[:, 0], Jd[:, -1] = D[0, :], D[-1, :], D[:, 0], D[:, -1]
+    n = 0
+    for r in range(D.shape[0]):
+        for c in range(D.shape[1]):
+            vals = [min(Jd[r + dr, c + dc], D[r, c]) for dr, dc in offsets
+                    if 0 <= r + dr < D.shape[0] and 0 <= c + dc < D.shape[1]]
+            n += bool(vals) and max(vals) > Jd[r, c]
+    return n
+
+
+def test_features_frontier_golden():
+    g = load("features_frontier.txt")
+    D = g["D"]
+    f = F.features(_frontier_image(D))
+    n = g["count_causal"]
+    assert np.isclose(f[22], n / D.size) and np.isclose(f[23], np.log1p(n))
+    # the fixture tells the causal set from the plausible wrong ones
+    anti = ((1, 1), (1, 0), (1, -1), (0, 1))
+    all8 = tuple((dr, dc) for dr in (-1, 0, 1) for dc in (-1, 0, 1) if (dr, dc) != (0, 0))
+    assert _count_with(D, anti) == g["count_anticausal"] != n
+    assert _count_with(D, all8) == g["count_all8"] != n
