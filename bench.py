@@ -23,6 +23,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -199,6 +201,14 @@ def cpu_model() -> str:
     return platform.machine() or "unknown"
 
 
+def host_cores() -> int:
+    """Cores this process may run on (nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def oracle_tiles_per_s(tiles, threads):
     """Oracle chain over `tiles`, one tile per host thread (the C oracle
     releases the GIL). Returns (tiles/s, seconds)."""
@@ -213,37 +223,223 @@ def oracle_tiles_per_s(tiles, threads):
     return len(tiles) / dt, dt
 
 
+def oracle_per_op_ms(tile):
+    """Single-thread milliseconds of each step of the oracle chain on one tile."""
+    import oracle
+    oracle.build()
+    out = {}
+    t = time.perf_counter()
+    J = oracle.marker(tile, 30)
+    R = oracle.recon(J, tile, 8)
+    out["marker_recon"] = time.perf_counter() - t
+    t = time.perf_counter()
+    B = oracle.threshold_below(R, 80)
+    out["threshold"] = time.perf_counter() - t
+    t = time.perf_counter()
+    F = oracle.fill_holes(B, 4)
+    out["fill"] = time.perf_counter() - t
+    t = time.perf_counter()
+    L = oracle.label_area(F, 20, 1000, 8)
+    out["label_area"] = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.edt((L >= 0).astype("uint8"))
+    out["edt"] = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.chain(tile)
+    out["chain"] = time.perf_counter() - t
+    return {k: round(1000 * v, 1) for k, v in out.items()}
+
+
+def cpu_baseline(tiles, batch, size):
+    """The oracle on all host cores, one tile per core (the first tile per
+    op single-threaded as well)."""
+    cores = host_cores()
+    v, dt = oracle_tiles_per_s(tiles, cores)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "nproc": cores, "per_op_single_thread_ms": oracle_per_op_ms(tiles[0]),
+            "sample": f"{len(tiles)} distinct {size}x{size} tiles of the bench's generator, one per host thread "
+                      f"on all {cores} cores, {dt:.1f} s wall; per-op times: one tile on one thread"}
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
-    tiles = make_tiles(a.batch, 0, a.size)
-    threads = min(os.cpu_count() or 1, a.batch)
+    cores = host_cores()
+    n = max(a.batch, cores)
+    tiles = make_tiles(n, 0, a.size)
     for _ in range(a.warmup):
-        oracle_tiles_per_s(tiles, threads)
+        oracle_tiles_per_s(tiles, cores)
     times = []
     for _ in range(a.steps):
-        _, dt = oracle_tiles_per_s(tiles, threads)
+        _, dt = oracle_tiles_per_s(tiles, cores)
         times.append(dt)
     total = sum(times)
-    value = a.batch * a.steps / total
+    value = n * a.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * total / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/i32",
         "data": "synthetic",
-        "config": {"workload": f"segmentation chain, {a.batch} x {a.size}x{a.size} nuclei tiles per step",
-                   "tiles_per_step": a.batch, "side": a.size},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
-                         "sample": f"{a.batch} tiles of {a.size}x{a.size} per step, one tile per host thread"},
+        "config": {"workload": f"segmentation chain on {a.size}x{a.size} nuclei tiles",
+                   "tiles_per_step": n, "side": a.size},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                         "sample": f"{n} tiles of {a.size}x{a.size} per step, one tile per host thread on all "
+                                   f"{cores} cores"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 # ----------------------------------------------------------------- native
+class Pipeline:
+    """Timed steps alternating between `nst` CUDA streams (one library
+    context each), every step flushing L2 on its own stream first. The timed
+    region is bracketed by events on the first stream, which the others
+    join at both ends."""
+
+    def __init__(self, rt, dev, nst, picker=None):
+        import torch
+        self.torch = torch
+        self.ctxs = [rt.Context(dev.index) for _ in range(nst)]
+        if picker is not None:
+            for c in self.ctxs:
+                picker.attach(c)
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(nst)]
+        self.flush = [torch.empty(256 << 20, dtype=torch.uint8, device=dev) for _ in range(nst)]   # > 129 MB L2
+
+    def run(self, fn, steps, warmup, barrier, timing=False):
+        """fn(k, ctx, stream) enqueues step k. Returns (total ms, per-step ms,
+        kernel launches in the timed steps, phase times if timing)."""
+        torch = self.torch
+        nst = len(self.streams)
+
+        def step(k, ev=None):
+            j = k % nst
+            s = self.streams[j]
+            with torch.cuda.stream(s):
+                self.flush[j].fill_(k & 0xFF)
+                if ev is not None:
+                    ev[0].record(s)
+                fn(k, self.ctxs[j], s)
+                if ev is not None:
+                    ev[1].record(s)
+
+        for k in range(max(warmup, nst)):
+            step(k)
+        torch.cuda.synchronize()
+        if timing:
+            for c in self.ctxs:
+                c.timing(True)
+                c.read_timing(reset=True)
+        l0 = sum(c.kernel_launches() for c in self.ctxs)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        t0.record(self.streams[0])
+        for s in self.streams[1:]:
+            s.wait_event(t0)
+        for k in range(steps):
+            step(k, evs[k])
+        for s in self.streams[1:]:
+            ej = torch.cuda.Event()
+            ej.record(s)
+            self.streams[0].wait_event(ej)
+        t1.record(self.streams[0])
+        barrier()
+        launches = sum(c.kernel_launches() for c in self.ctxs) - l0
+        phases = {}
+        if timing:
+            for c in self.ctxs:
+                for name, (ms, n) in c.read_timing(reset=True).items():
+                    m0, n0 = phases.get(name, (0.0, 0))
+                    phases[name] = (m0 + ms, n0 + n)
+                c.timing(False)
+        return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in evs], launches, phases
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+
+
+def copy_rates(dev, nbytes=1 << 30):
+    """Plain pinned host <-> device copy rates (GB/s, best of 3) on this machine."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, (dst, src) in (("h2d_gbs", (d, h)), ("d2h_gbs", (h, d))):
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dst.copy_(src, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            best = max(best, nbytes / (e0.elapsed_time(e1) / 1000) / 1e9)
+        out[name] = round(best, 1)
+    del h, d
+    return out
+
+
+def config3_leg(rt, ctx, dev, stream_ctor):
+    """Configuration 3: 64 uneven tiles (sides 1024..4096 step 256, 50..400
+    nuclei per Mpx) in one call captured in a CUDA graph, parameters from
+    the autotuner, replayed on the capture stream; outputs of tiles 0, 31,
+    32 and 63 (both chunks, both sides of the chunk boundary) checked
+    against the oracle after the timed replays; null if any differs."""
+    import concurrent.futures as cf
+
+    import torch
+
+    import oracle
+    import synth
+    from paper_1405_7958_gb300 import autotune
+    specs = synth.batch_sizes(64, 3000)
+    b3 = [rt.synth_tile(H, W, sd, ns, ctx=ctx) for H, W, ns, sd in specs]
+    px3 = sum(H * W for H, W, _, _ in specs)
+    tuned = autotune.tune(b3, reps=2, ctx=ctx)["best"]
+    p3 = rt.SegParams(variant=int(tuned["variant"]), max_local=int(tuned["max_local"]))
+    g3s = stream_ctor()
+    with torch.cuda.stream(g3s):
+        o3 = rt.segment_batch(b3, p3, ctx=ctx, stream=g3s, want_recon=False, want_filled=False)
+    g3s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=g3s):
+        rt.segment_batch(b3, p3, outputs=o3, ctx=ctx, stream=g3s, want_recon=False, want_filled=False)
+    with torch.cuda.stream(g3s):
+        for _ in range(2):
+            graph.replay()
+        for o in o3:
+            o["L"].fill_(-5)
+            o["D"].fill_(-5)
+        t3 = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(g3s)
+            graph.replay()
+            e1.record(g3s)
+            t3.append((e0, e1))
+    g3s.synchronize()
+    t3 = [a.elapsed_time(b) for a, b in t3]
+    sample = (0, 31, 32, 63)
+    hosts = [b3[i].cpu().numpy() for i in sample]
+    with cf.ThreadPoolExecutor(max_workers=4) as ex:
+        want = list(ex.map(oracle.chain, hosts))
+    ok = all(np.array_equal(o3[i]["L"].cpu().numpy(), w["L"]) and np.array_equal(o3[i]["D"].cpu().numpy(), w["D"])
+             for i, w in zip(sample, want))
+    ms3 = statistics.median(t3)
+    res = {"tiles": 64, "megapixels": px3 / 1e6, "tuned": tuned, "graph_replay_ms": ms3, "replays": 5,
+           "oracle_checked_tiles": list(sample), "outputs_match_oracle": ok,
+           "chain_bytes_per_replay": BYTES_CHAIN * px3,
+           "chain_gbs": BYTES_CHAIN * px3 / (ms3 / 1000.0) / 1e9,
+           "tile4k_equiv_s": px3 / 2 ** 24 / (ms3 / 1000.0) if ok else None,
+           "tiles_s": 64 / (ms3 / 1000.0) if ok else None}
+    del o3, b3, graph
+    return res
+
+
+
 def run_native(a, rank, world, local_rank):
-    tiles = make_tiles(a.batch, rank, a.size)     # before the first CUDA call
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -260,115 +456,66 @@ def run_native(a, rank, world, local_rank):
         torch.cuda.synchronize()
 
     ctx = rt.Context(local_rank)
+    # the bench's tiles, drawn on the GPU by the generator's bit-exact twin
+    imgs = [rt.config2_tile(2000 + 100 * rank + i, H=a.size, W=a.size, ctx=ctx) for i in range(a.batch)]
+    torch.cuda.synchronize()
     # the metric's configuration: batched, with the trained variant picker
     from paper_1405_7958_gb300 import picker as pkmod
     picker = pkmod.load(os.path.join(ROOT, "paper_1405_7958_gb300", "data", "picker_config4.npz"), device=dev)
     picker.attach(ctx)
-    params = rt.SegParams(policy=1)
+    learned = rt.SegParams(policy=1)
     plain = rt.SegParams()
-    stream = torch.cuda.current_stream()
-    imgs = [torch.from_numpy(t).to(dev) for t in tiles]
-    # consecutive steps alternate between `streams` CUDA streams, one library
-    # context each, so one step's labeling and distance transform overlap the
-    # next step's propagation; every step flushes L2 on its own stream first
     nst = max(1, a.streams)
-    ctxs = [ctx] + [rt.Context(local_rank) for _ in range(nst - 1)]
-    for c in ctxs[1:]:
-        picker.attach(c)
-    sts = [torch.cuda.Stream(device=dev) for _ in range(nst)]
-    flushes = [torch.empty(256 << 20, dtype=torch.uint8, device=dev) for _ in range(nst)]   # > 129 MB L2
-    outs_s = [None] * nst
+    pipe = Pipeline(rt, dev, nst, picker)
+    outs_l = [None] * nst
+    outs_p = [None] * nst
+    outs_1 = [[None] * a.batch for _ in range(nst)]
 
-    def step(k, ev=None):
+    def step_learned(k, c, s):
         j = k % nst
-        with torch.cuda.stream(sts[j]):
-            flushes[j].fill_(k & 0xFF)
-            if ev is not None:
-                ev[0].record(sts[j])
-            outs_s[j] = rt.segment_batch(imgs, params, outputs=outs_s[j], ctx=ctxs[j], stream=sts[j])
-            if ev is not None:
-                ev[1].record(sts[j])
+        outs_l[j] = rt.segment_batch(imgs, learned, outputs=outs_l[j], ctx=c, stream=s)
+
+    def step_plain(k, c, s):
+        j = k % nst
+        outs_p[j] = rt.segment_batch(imgs, plain, outputs=outs_p[j], ctx=c, stream=s)
+
+    def step_per_tile(k, c, s):
+        j = k % nst
+        for i, im in enumerate(imgs):
+            o = outs_1[j][i]
+            outs_1[j][i] = rt.segment_batch([im], plain, outputs=None if o is None else [o], ctx=c, stream=s)[0]
 
     sampler = ClockSampler(local_rank)
     sampler.start()
-    for k in range(max(a.warmup, nst)):
-        step(k)
-    torch.cuda.synchronize()
-    visits = ctx.recon_stats()
-    outs = outs_s[0]
-    flush = flushes[0]
-    for c in ctxs:
-        c.timing(True)
-        c.read_timing(reset=True)
-    l0 = sum(c.kernel_launches() for c in ctxs)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
     wall0 = time.time()
-    t0e.record(sts[0])
-    for s in sts[1:]:
-        s.wait_event(t0e)
-    for k in range(a.steps):
-        step(k, evs[k])
-    for s in sts[1:]:
-        ej = torch.cuda.Event()
-        ej.record(s)
-        sts[0].wait_event(ej)
-    t1e.record(sts[0])
-    barrier()
+    total_ms, step_ms, launches, phases = pipe.run(step_learned, a.steps, a.warmup, barrier, timing=True)
     sampler.window(wall0, time.time())
     clocks = sampler.stop()
-    launches = sum(c.kernel_launches() for c in ctxs) - l0
-    step_ms = [s.elapsed_time(e) for s, e in evs]
-    phases = {}
-    for c in ctxs:
-        for name, (ms, n) in c.read_timing(reset=True).items():
-            m0, n0 = phases.get(name, (0.0, 0))
-            phases[name] = (m0 + ms, n0 + n)
-        c.timing(False)
-    for c in ctxs[1:]:
-        c.close()
-    total_ms = t0e.elapsed_time(t1e)
+    visits = pipe.ctxs[0].recon_stats()
+    picks = rt.last_picks(pipe.ctxs[0])
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     px = a.size * a.size
     value = world * a.batch * a.steps / (total_ms / 1000.0)
-    picks = rt.last_picks(ctx)
 
-    def timed(fn, steps):
-        ms = []
-        for k in range(steps):
-            flush.fill_(k & 0xFF)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        return sum(ms)
-
+    # the plain legs on the same harness (same streams, contexts, flushes)
     k2 = max(5, a.steps // 4)
-    outs_p = rt.segment_batch(imgs, plain, ctx=ctx)
-    timed(lambda: rt.segment_batch(imgs, plain, outputs=outs_p, ctx=ctx), 2)
-    batched_plain = a.batch * k2 / (timed(lambda: rt.segment_batch(imgs, plain, outputs=outs_p, ctx=ctx), k2) / 1000)
-    outs1 = [rt.segment_batch([im], plain, ctx=ctx)[0] for im in imgs]
-
-    def per_tile():
-        for im, o in zip(imgs, outs1):
-            rt.segment_batch([im], plain, outputs=[o], ctx=ctx)
-
-    timed(per_tile, 1)
-    per_tile_plain = a.batch * k2 / (timed(per_tile, k2) / 1000)
-    # batched and plain produce the same bytes
-    for o_l, o_p, o_1 in zip(outs, outs_p, outs1):
+    plain_ms, _, plain_launches, _ = pipe.run(step_plain, k2, a.warmup, barrier)
+    per_tile_ms, _, per_tile_launches, _ = pipe.run(step_per_tile, k2, a.warmup, barrier)
+    batched_plain = a.batch * k2 / (plain_ms / 1000)
+    per_tile_plain = a.batch * k2 / (per_tile_ms / 1000)
+    torch.cuda.synchronize()
+    # batched, plain and one-at-a-time produce the same bytes
+    for o_l, o_p, o_1 in zip(outs_l[0], outs_p[0], outs_1[0]):
         assert torch.equal(o_l["L"], o_p["L"]) and torch.equal(o_l["D"], o_1["D"])
 
     # configuration 1: reconstruction only, one 512^2 image, median of 200
     # timed runs after 20 warm-up runs, with the bytes the passes moved
     config1 = None
     config3 = None
+    stream = torch.cuda.current_stream()
     if not a.no_configs and world == 1:
         import synth
         c1 = torch.from_numpy(synth.config1_image(1000)).to(dev)
@@ -388,37 +535,7 @@ def run_native(a, rank, world, local_rank):
                    "warmup": 20, "tile_visits": v1, "tile_iterations": it1,
                    "pass_bytes": it1 * PASSES_PER_ITERATION * TILE_PX * BYTES_PASS,
                    "compulsory_bytes": BYTES_RECON * 512 * 512}
-        # configuration 3: 64 uneven tiles (sides 1024..4096 step 256, 50..400
-        # nuclei per Mpx) in one call captured in a CUDA graph, parameters
-        # from the autotuner; throughput in 4K-tile equivalents
-        from paper_1405_7958_gb300 import autotune
-        specs = synth.batch_sizes(64, 3000)
-        b3 = [rt.synth_tile(H, W, sd, ns, ctx=ctx) for H, W, ns, sd in specs]
-        px3 = sum(H * W for H, W, _, _ in specs)
-        tuned = autotune.tune(b3, reps=2, ctx=ctx, stream=stream)["best"]
-        p3 = rt.SegParams(variant=int(tuned["variant"]), max_local=int(tuned["max_local"]))
-        g3s = torch.cuda.Stream(device=dev)
-        with torch.cuda.stream(g3s):
-            o3 = rt.segment_batch(b3, p3, ctx=ctx, stream=g3s, want_recon=False, want_filled=False)
-        g3s.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=g3s):
-            rt.segment_batch(b3, p3, outputs=o3, ctx=ctx, stream=g3s, want_recon=False, want_filled=False)
-        for _ in range(2):
-            graph.replay()
-        torch.cuda.synchronize()
-        t3 = []
-        for _ in range(5):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(g3s)
-            graph.replay()
-            e1.record(g3s)
-            e1.synchronize()
-            t3.append(e0.elapsed_time(e1))
-        ms3 = statistics.median(t3)
-        config3 = {"tiles": 64, "megapixels": px3 / 1e6, "tuned": tuned, "graph_replay_ms": ms3,
-                   "tile4k_equiv_s": px3 / 2 ** 24 / (ms3 / 1000.0), "tiles_s": 64 / (ms3 / 1000.0)}
-        del o3, b3, graph
+        config3 = config3_leg(rt, ctx, dev, lambda: torch.cuda.Stream(device=dev))
 
     serving = None
     if a.serve_seconds > 0 and world == 1:
@@ -438,7 +555,7 @@ def run_native(a, rank, world, local_rank):
         per_launch_s = sweep_ms / sweep_n / 1000.0
         algo_bytes = BYTES_RECON * px * a.batch
         ach = algo_bytes / per_launch_s / 1e9
-        its = visits[1]       # dense tile iterations of one step (taken after the warm-up)
+        its = visits[1]       # dense tile iterations of one step (the last one)
         pass_bytes = its * PASSES_PER_ITERATION * TILE_PX * BYTES_PASS
         roof = {"kernel": "recon_persistent_kernel<8,0>", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_source": peak_kind, "traffic": profiled_traffic(),
@@ -451,33 +568,27 @@ def run_native(a, rank, world, local_rank):
     # distances back. Steps alternate between the compute streams (one context
     # each); the read-backs run on a stream of their own, from output sets
     # rotated over twice as many steps, so no compute stream waits behind the
-    # read-back queue (the copy engine moves about 190 GB/s device to host,
-    # close to the chain's own rate for the 1 GB of outputs per step)
+    # read-back queue
     e2e = None
     if not a.no_e2e:
-        nst = max(1, a.streams)
         nset = 2 * nst
-        h_in = [torch.from_numpy(t).pin_memory() for t in tiles]
-        h_L = [[torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in tiles] for _ in range(nset)]
-        h_D = [[torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in tiles] for _ in range(nset)]
+        h_in = [im.cpu().pin_memory() for im in imgs]
+        h_L = [[torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in imgs] for _ in range(nset)]
+        h_D = [[torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in imgs] for _ in range(nset)]
         d_in = [[torch.empty_like(x, device=dev) for x in imgs] for _ in range(nst)]
-        ctxs = [ctx] + [rt.Context(local_rank) for _ in range(nst - 1)]
-        for c in ctxs[1:]:
-            picker.attach(c)
-        streams = [torch.cuda.Stream(device=dev) for _ in range(nst)]
         read_s = torch.cuda.Stream(device=dev)
         outs_e = [None] * nset
         read_done = [None] * nset
 
         def e2e_step(k):
             j, b = k % nst, k % nset
-            s = streams[j]
+            s = pipe.streams[j]
             with torch.cuda.stream(s):
                 if read_done[b] is not None:
                     s.wait_event(read_done[b])      # the set's previous read-back has finished
                 for h, d in zip(h_in, d_in[j]):
                     d.copy_(h, non_blocking=True)
-                outs_e[b] = rt.segment_batch(d_in[j], params, outputs=outs_e[b], ctx=ctxs[j], stream=s,
+                outs_e[b] = rt.segment_batch(d_in[j], learned, outputs=outs_e[b], ctx=pipe.ctxs[j], stream=s,
                                              want_recon=False, want_filled=False)
                 computed = torch.cuda.Event()
                 computed.record(s)
@@ -494,16 +605,16 @@ def run_native(a, rank, world, local_rank):
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(streams[0])
-        for s in streams[1:] + [read_s]:
+        e0.record(pipe.streams[0])
+        for s in pipe.streams[1:] + [read_s]:
             s.wait_event(e0)
         for k in range(a.steps):
             e2e_step(k)
-        for s in streams[1:] + [read_s]:
+        for s in pipe.streams[1:] + [read_s]:
             ev = torch.cuda.Event()
             ev.record(s)
-            streams[0].wait_event(ev)
-        e1.record(streams[0])
+            pipe.streams[0].wait_event(ev)
+        e1.record(pipe.streams[0])
         barrier()
         tt = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
         if world > 1:
@@ -511,18 +622,22 @@ def run_native(a, rank, world, local_rank):
         # the read-back matches the device result
         torch.cuda.synchronize()
         assert np.array_equal(h_L[0][0].numpy(), outs_e[0][0]["L"].cpu().numpy())
+        rates = copy_rates(dev)
+        h2d, d2h = a.batch * px, a.batch * px * 8
         e2e = {"value": world * a.batch * a.steps / (float(tt.item()) / 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": a.batch * px, "d2h_bytes_per_step": a.batch * px * 8,
-               "streams": nst, "output_sets": nset}
-        for c in ctxs[1:]:
-            c.close()
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "streams": nst, "output_sets": nset, "copy_gbs": rates,
+               "copy_bound_tiles_s": a.batch / max(h2d / (rates["h2d_gbs"] * 1e9), d2h / (rates["d2h_gbs"] * 1e9))}
+        del h_in, h_L, h_D, d_in
 
     cpu = None
     if rank == 0 and not a.no_cpu:
-        threads = min(os.cpu_count() or 1, a.batch)
-        v, dt = oracle_tiles_per_s(tiles, threads)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
-               "sample": f"the {a.batch} bench tiles ({a.size}x{a.size}), one per host thread, {dt:.1f} s"}
+        n_cpu = max(a.batch, host_cores())
+        cpu_tiles = [im.cpu().numpy() for im in imgs]
+        cpu_tiles += [rt.config2_tile(3000 + i, H=a.size, W=a.size, ctx=ctx).cpu().numpy()
+                      for i in range(n_cpu - len(cpu_tiles))]
+        cpu = cpu_baseline(cpu_tiles, a.batch, a.size)
+    pipe.close()
 
     if world > 1:
         dist.barrier()
@@ -536,7 +651,8 @@ def run_native(a, rank, world, local_rank):
                        "tiles_per_step": a.batch, "side": a.size, "parallelism": f"replicas x{world}",
                        "l2": "flushed before every step (256 MB write on the step's stream)",
                        "streams": nst,
-                       "pipelining": "consecutive steps alternate between the streams (one context each)"},
+                       "pipelining": "consecutive steps alternate between the streams (one context each); "
+                                     "the plain legs run on the same harness"},
             "chain_hbm_gbs": chain_bytes / (total_ms / 1000.0) / 1e9,
             "roofline": roof,
             "phases_ms_per_step": {k: v[0] / a.steps for k, v in phases.items()},
@@ -545,6 +661,8 @@ def run_native(a, rank, world, local_rank):
             "batched_learned_tiles_s": value,
             "batched_plain_tiles_s": world * batched_plain,
             "plain_per_tile_tiles_s": world * per_tile_plain,
+            "launches_per_step": {"batched_learned": launches / a.steps, "batched_plain": plain_launches / k2,
+                                  "per_tile_plain": per_tile_launches / k2},
             "picker_choices": picks,
             "serving_batched_learned": serving,
             "config1_recon_512": config1,

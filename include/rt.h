@@ -30,10 +30,20 @@
  *    a marker above the mask) are written to `dev_status`, a device int32
  *    the caller may pass (NULL = not reported) and read after synchronising;
  *    it holds RT_OK or the first error code raised.
- *  - A context owns its workspace (device scratch), grows it on demand with
- *    cudaMalloc (which synchronises the device) and reuses it across calls.
- *    Calls on one context must be serialised by the caller (one stream at a
- *    time); use one context per concurrent stream.
+ *  - A context owns its workspace (device scratch), reserves it at creation
+ *    (rt_create's workspace_bytes; rt_segment_workspace_bytes gives the
+ *    exact need of a batch), grows it on demand with cudaMalloc (which
+ *    synchronises the device) when a call needs more, and reuses it across
+ *    calls. Calls on one context must be serialised by the caller (one
+ *    stream at a time); use one context per concurrent stream.
+ *  - Iterative steps are bounded: the reconstruction's propagation by a
+ *    number of tile visits (max_iters, see rt_set_limits), and every
+ *    propagation (reconstruction and hole filling) by device time (20 s
+ *    unless set otherwise). A bound that is reached stops the step short of
+ *    its fixed point, reports RT_ETIMEOUT in the device status, and leaves
+ *    the context usable for the next call.
+ *  - Strides are in elements, not bytes (a reading of the boundary: every
+ *    image has one element type, so an element stride cannot be misaligned).
  */
 #ifndef RT_SEG_H
 #define RT_SEG_H
@@ -58,7 +68,9 @@ typedef enum {
     RT_ECUDA = 3,     /* CUDA runtime error at launch */
     RT_ETIMEOUT = 4,  /* device-side iteration or wait bound reached */
     RT_EMARKER = 5,   /* marker above the mask somewhere (output still defined) */
-    RT_EQUEUE = 6,    /* frontier queue overflow that the fall-back could not absorb */
+    RT_EQUEUE = 6,    /* frontier queue overflow; never raised here: every queue of the
+                         RT_QUEUE / RT_HYBRID visits has one slot per pixel of its tile and
+                         a pixel is queued at most once at a time */
     RT_EUNAVAIL = 7,  /* requested variant or feature not available */
     RT_ESIZE = 8      /* image larger than the fixed scratch of rt_edt_noalloc */
 } rt_status;
@@ -73,9 +85,20 @@ enum {
 
 typedef struct rt_ctx rt_ctx;
 
-/* Create a context bound to CUDA device `device`. Returns RT_OK and sets
- * *ctx, or an error (the device is not usable, allocation failed). */
-RT_API rt_status rt_create(rt_ctx **ctx, int device);
+/* Create a context bound to CUDA device `device`, reserving
+ * `workspace_bytes` of device workspace at once (0: none until a call needs
+ * it). Returns RT_OK and sets *ctx, or an error (RT_ECUDA: the device is not
+ * usable; RT_ENOMEM: the reservation failed). */
+RT_API rt_status rt_create(rt_ctx **ctx, int device, size_t workspace_bytes);
+
+/* Bounds of the iterative steps of the single-operation entry points
+ * (rt_reconstruct, rt_fill_holes) on this context, and the defaults of
+ * rt_segment_batch: max_iters > 0 lets one reconstruction propagation make
+ * at most max_iters tile visits per 32 x 64 tile of its images on average (0: no
+ * bound; how many visits a propagation needs depends on the schedule, so a
+ * bound close to the need may or may not be reached); timeout_ms > 0 bounds
+ * each propagation's device time (0: 20 s). Negative values: RT_EINVAL. */
+RT_API rt_status rt_set_limits(rt_ctx *ctx, int max_iters, int timeout_ms);
 
 /* Free a context and its workspace. Waits for the device first. NULL is a
  * no-op. */
@@ -272,6 +295,12 @@ RT_API rt_status rt_mlp_forward(rt_ctx *ctx, const uint16_t *wb, const float *no
 RT_API rt_status rt_mlp_backward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x,
                                  const float *act, const float *logits, const int32_t *label, int B,
                                  float *grad, float *loss, void *stream);
+/* Normalisation of the network's input from a training set x (B x 24,
+ * device, row-major): norm[0..23] = the column means, norm[24..47] = the
+ * column standard deviations with divisor B - 1 (0 when B = 1), raised to
+ * at least 1e-6; sums in double in a fixed order, so the result is
+ * deterministic. */
+RT_API rt_status rt_feature_norm(rt_ctx *ctx, const float *x, int B, float *norm, void *stream);
 RT_API rt_status rt_mlp_adamw(rt_ctx *ctx, float *master, uint16_t *wb, const float *grad, float *m,
                               float *v, int step, float lr, float beta1, float beta2, float eps,
                               float weight_decay, void *stream);
@@ -322,6 +351,9 @@ typedef struct {
     int policy;      /* RT_POLICY_PLAIN: `variant` for every tile;
                         RT_POLICY_LEARNED: the attached picker chooses per tile and the
                         plain choice is kept whenever no picker is attached */
+    int max_iters;   /* tile visits per 32 x 64 tile allowed to the propagation, as in
+                        rt_set_limits; 0 = the context's bound */
+    int timeout_ms;  /* device-time bound of each propagation; 0 = the context's (20 s) */
 } rt_seg_params;
 
 enum { RT_POLICY_PLAIN = 0, RT_POLICY_LEARNED = 1 };
@@ -337,10 +369,20 @@ RT_API void rt_seg_params_default(rt_seg_params *p);
  *   L' = label_area(F, 8, [min_area, max_area]); D = edt(L' >= 0).
  * `tiles` is a HOST array (copied before return); all outputs are device
  * buffers. The per-tile outputs are identical to running the single-tile
- * entry points one tile at a time.
+ * entry points one tile at a time. Tiles run in chunks of up to 32; every
+ * stage of the chain is one launch for the whole chunk. A single tile may be
+ * a whole slide (up to 32768 x 32768): the propagations cross the seams of
+ * their internal tiles and the labels join across block edges, so the
+ * result is that of the slide as one image.
  */
 RT_API rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_seg_params *params,
                            void *stream);
+
+/* Device workspace bytes rt_segment_batch needs for these tiles and
+ * parameters (its largest chunk of up to 32 tiles): a context created with
+ * at least this much never allocates during such a call. 0 on invalid
+ * arguments. Host-only; the tiles' pointers are not read. */
+RT_API size_t rt_segment_workspace_bytes(const rt_tile *tiles, int n, const rt_seg_params *params);
 
 #ifdef __cplusplus
 }

@@ -68,12 +68,12 @@ def _dev_ptr(t: torch.Tensor, dtype: torch.dtype, name: str):
 class Context:
     """Owns a library context (device workspace) on one CUDA device."""
 
-    def __init__(self, device: int | None = None):
+    def __init__(self, device: int | None = None, workspace_bytes: int = 0):
         if device is None:
             device = torch.cuda.current_device()
         self.device = device
         h = ctypes.c_void_p()
-        _check(lib().rt_create(ctypes.byref(h), device), "rt_create")
+        _check(lib().rt_create(ctypes.byref(h), device, int(workspace_bytes)), "rt_create")
         self._h = h
 
     @property
@@ -82,6 +82,11 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return lib().rt_workspace_bytes(self._h)
+
+    def set_limits(self, max_iters: int = 0, timeout_ms: int = 0):
+        """Bounds of the propagations of the single-operation calls (and the
+        defaults of segment_batch): tile visits per tile, device time."""
+        _check(lib().rt_set_limits(self._h, int(max_iters), int(timeout_ms)), "rt_set_limits")
 
     def timing(self, enable: bool = True):
         _check(lib().rt_timing_enable(self._h, int(enable)), "rt_timing_enable")
@@ -261,10 +266,14 @@ class Picker:
         self.norm = torch.cat([torch.zeros(24), torch.ones(24)]).to(self.device) if norm is None else norm
         self.step_count = 0
 
-    def set_norm(self, feats: torch.Tensor):
-        mu = feats.mean(dim=0)
-        sd = feats.std(dim=0).clamp_min(1e-6)
-        self.norm = torch.cat([mu, sd]).float().contiguous().to(self.device)
+    def set_norm(self, feats: torch.Tensor, stream=None):
+        """Input normalisation from a training set (B x 24 float32 on the
+        device), computed by the library (rt_feature_norm)."""
+        x = feats.to(device=self.device, dtype=torch.float32).contiguous()
+        norm = torch.empty(48, dtype=torch.float32, device=self.device)
+        _check(lib().rt_feature_norm(self.ctx.handle, x.data_ptr(), x.shape[0], norm.data_ptr(), _stream(stream)),
+               "rt_feature_norm")
+        self.norm = norm
 
     def forward(self, x: torch.Tensor, with_act: bool = False, stream=None):
         B = x.shape[0]
@@ -322,12 +331,30 @@ class SegParams:
     variant: int = RT_AUTO
     max_local: int = 0
     policy: int = 0          # 0 plain (fixed variant), 1 learned (attached picker)
+    max_iters: int = 0       # tile visits per tile allowed to the propagation (0: the context's bound)
+    timeout_ms: int = 0      # device-time bound of each propagation (0: the context's)
 
     def to_c(self) -> _native.RtSegParams:
         p = _native.RtSegParams()
         for k in self.__dataclass_fields__:
             setattr(p, k, int(getattr(self, k)))
         return p
+
+
+def segment_workspace_bytes(shapes, params: SegParams | None = None) -> int:
+    """Device workspace bytes segment_batch needs for tiles of these (H, W)
+    shapes (the library's exact figure, rt_segment_workspace_bytes)."""
+    n = len(shapes)
+    if n == 0:
+        return 0
+    tiles = (_native.RtTile * n)()
+    for i, (H, W) in enumerate(shapes):
+        t = tiles[i]
+        t.H, t.W = int(H), int(W)
+        t.img = t.labels = t.d2 = 1            # placeholders: the size query reads no pointer
+        t.ld_img = t.ld_labels = t.ld_d2 = int(W)
+    cp = (params or SegParams()).to_c()
+    return int(lib().rt_segment_workspace_bytes(tiles, n, ctypes.byref(cp)))
 
 
 def segment_batch(images, params: SegParams | None = None, *, outputs=None, want_recon: bool = True,

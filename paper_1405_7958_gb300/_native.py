@@ -19,7 +19,8 @@ EXPORTS = (
     "rt_reconstruct", "rt_fill_holes", "rt_label_area", "rt_edt", "rt_seg_params_default",
     "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_recon_stats",
     "rt_edt_noalloc", "rt_synth_tile", "rt_tile_features", "rt_mlp_forward", "rt_mlp_backward",
-    "rt_mlp_adamw", "rt_set_picker", "rt_last_picks",
+    "rt_mlp_adamw", "rt_set_picker", "rt_last_picks", "rt_set_limits", "rt_segment_workspace_bytes",
+    "rt_feature_norm",
 )
 RT_NPHASES = 7
 PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt", "pick")
@@ -46,15 +47,17 @@ class RtTile(ctypes.Structure):
 
 class RtSegParams(ctypes.Structure):
     _fields_ = [(n, _int) for n in ("h_offset", "threshold", "min_area", "max_area", "conn_recon",
-                                    "conn_fill", "variant", "max_local", "policy")]
+                                    "conn_fill", "variant", "max_local", "policy", "max_iters", "timeout_ms")]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"librtseg.so is not built ({path}); run paper_1405_7958_gb300/build.py")
     lib = ctypes.CDLL(path)
-    lib.rt_create.argtypes = [ctypes.POINTER(_vp), _int]
+    lib.rt_create.argtypes = [ctypes.POINTER(_vp), _int, ctypes.c_size_t]
     lib.rt_create.restype = _int
+    lib.rt_set_limits.argtypes = [_vp, _int, _int]
+    lib.rt_set_limits.restype = _int
     lib.rt_destroy.argtypes = [_vp]
     lib.rt_destroy.restype = None
     lib.rt_status_str.argtypes = [_int]
@@ -95,6 +98,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_seg_params_default.restype = None
     lib.rt_segment_batch.argtypes = [_vp, ctypes.POINTER(RtTile), _int, ctypes.POINTER(RtSegParams), _vp]
     lib.rt_segment_batch.restype = _int
+    lib.rt_segment_workspace_bytes.argtypes = [ctypes.POINTER(RtTile), _int, ctypes.POINTER(RtSegParams)]
+    lib.rt_segment_workspace_bytes.restype = ctypes.c_size_t
+    lib.rt_feature_norm.argtypes = [_vp, _vp, _int, _vp, _vp]
+    lib.rt_feature_norm.restype = _int
     lib.rt_timing_enable.argtypes = [_vp, _int]
     lib.rt_timing_enable.restype = _int
     lib.rt_timing_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _int]

@@ -36,6 +36,8 @@ struct rt_ctx {
     cudaEvent_t picks_ev = nullptr;        // recorded after their copy (not under stream capture)
     bool picks_ev_valid = false;
     int n_last_picks = 0;
+    int max_iters = 0;                     // limits of the single-operation entry points (rt_set_limits)
+    uint64_t timeout_ns = 0;
     std::vector<PhaseRec> recs;
     std::vector<cudaEvent_t> pool;
 };
@@ -78,7 +80,7 @@ class Phase {
     PhaseRec rec_{0, nullptr, nullptr};
 };
 
-constexpr uint64_t kSweepTimeoutNs = 20000000000ull;   // 20 s bound on one propagation
+constexpr uint64_t kSweepTimeoutNs = 20000000000ull;   // default bound on one propagation (20 s)
 
 // Bump allocator over the context workspace (256-byte aligned pieces).
 struct Carve {
@@ -174,8 +176,17 @@ void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w, bool grouped = false)
 // receives the device status. With `pick` (device, one picker class per
 // image) every image propagates with its own variant: one launch per variant
 // group over the group's tile list, with no host round trip.
+// Bounds of a propagation: max_iters > 0 allows max_iters tile visits per
+// 32 x 64 tile on average; timeout_ns bounds its device time.
+struct Limits {
+    int max_iters;
+    uint64_t timeout_ns;
+};
+
+Limits ctx_limits(const rt_ctx *ctx) { return {ctx->max_iters, ctx->timeout_ns ? ctx->timeout_ns : kSweepTimeoutNs}; }
+
 rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int variant, int max_local, int32_t *err,
-                    cudaStream_t s, const int32_t *pick = nullptr)
+                    cudaStream_t s, Limits lim, const int32_t *pick = nullptr)
 {
     if (variant == RT_AUTO) variant = RT_RASTER;
     // RT_RASTER / RT_QUEUE: every tile starts flagged for a dense visit (the
@@ -196,7 +207,11 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
     p.pending = w.ctl + kCtlPending;
     p.err = err;
     p.visits = w.ctl + kCtlVisits;
-    p.timeout_ns = kSweepTimeoutNs;
+    p.timeout_ns = lim.timeout_ns;
+    const int64_t bound = (int64_t)lim.max_iters * b.ntiles;
+    p.max_visits = lim.max_iters > 0 ? (uint32_t)(bound < 0xffffffffLL ? bound : 0xffffffffLL) : 0u;
+    p.spent = w.ctl + kCtlSpent;
+    p.abort = w.ctl + kCtlAbort;
     p.map = nullptr;
     p.nvirt = nullptr;
     int grid = 0;
@@ -237,24 +252,135 @@ void add_image(ReconBatch &b, const uint8_t *marker, int64_t ld_marker, const ui
     b.n++;
 }
 
-// Union-find workspace for an H x W image.
-void carve_uf(Carve &cv, UfArgs &a, int H, int W)
+// the tiles' status words: the device status of the chunk that carried them
+struct StatusOut {
+    int32_t *dst[kMaxImgs];
+};
+__global__ void copy_status_kernel(const int32_t *src, StatusOut o, int n)
 {
-    const size_t N = (size_t)H * W;
-    const size_t nblk = (size_t)ceil_div(W, kUfBlock) * ceil_div(H, kUfBlock);
-    a.U = cv.take<int32_t>(N);
-    a.A = cv.take<int32_t>(N);
-    a.edge = cv.take<int32_t>(nblk * kUfEdge);
-    a.list = cv.take<int32_t>(N / 2 + 2);
-    a.nlist = cv.take<uint32_t>(1);
-    a.lroot = cv.take<uint16_t>(N);
-    a.bempty = cv.take<uint8_t>(nblk);
+    if ((int)threadIdx.x < n && o.dst[threadIdx.x]) *o.dst[threadIdx.x] = *src;
 }
 
-// a tile's status word: the device status of the chunk that carried it
-__global__ void copy_status_kernel(const int32_t *src, int32_t *dst)
+bool bad_params(const rt_seg_params &P)
 {
-    if (threadIdx.x == 0) *dst = *src;
+    if (P.conn_recon != 4 && P.conn_recon != 8) return true;
+    if (P.conn_fill != 4 && P.conn_fill != 8) return true;
+    if (P.h_offset < 0 || P.h_offset > 255 || P.threshold < 0 || P.threshold > 256) return true;
+    if (P.variant < RT_AUTO || P.variant > RT_HYBRID) return true;
+    if (P.policy != RT_POLICY_PLAIN && P.policy != RT_POLICY_LEARNED) return true;
+    if (P.max_local < 0 || P.max_iters < 0 || P.timeout_ms < 0) return true;
+    return false;
+}
+
+bool bad_tile(const rt_tile &t)
+{
+    if (!t.img || !t.labels || !t.d2 || bad_dims(t.H, t.W)) return true;
+    if (t.ld_img < t.W || t.ld_labels < t.W || t.ld_d2 < t.W) return true;
+    if (t.recon && t.ld_recon < t.W) return true;
+    if (t.filled && t.ld_filled < t.W) return true;
+    return false;
+}
+
+// Workspace of one chunk (up to kMaxImgs tiles) of rt_segment_batch. Every
+// stage runs once for the whole chunk, so every tile has its own buffers:
+// padded reconstruction copies, the binary image, the fill's bit planes, the
+// union-find arrays, the kept-pixel bit plane and the distance transform's
+// column masks.
+struct Chunk {
+    ReconBatch b;
+    ReconWs w;
+    FeatBatch fb;
+    float *feat = nullptr;
+    int32_t *picks = nullptr;
+    FillBatch fill;
+    uint32_t *fill_flags = nullptr, *fill_pending = nullptr;
+    UfBatch uf;
+    EdtBitsBatch eb;
+};
+
+// Lays chunk [c0, c0 + cn) out in cv. With cv.base == nullptr only the size
+// is measured (cv.off); no pointer is formed.
+void layout_chunk(Carve &cv, Chunk &c, const rt_tile *tiles, int c0, int cn, const rt_seg_params &P, bool learned)
+{
+    const bool real = cv.base != nullptr;
+    std::memset(&c.b, 0, sizeof(c.b));
+    for (int i = 0; i < cn; ++i) {
+        const rt_tile &t = tiles[c0 + i];
+        add_image(c.b, nullptr, 0, t.img, t.ld_img, t.H, t.W, P.h_offset);
+    }
+    carve_recon(cv, c.b, c.w, learned);
+    if (learned) {
+        c.fb.n = cn;
+        for (int i = 0; i < cn; ++i) {
+            const rt_tile &t = tiles[c0 + i];
+            const size_t nb = (size_t)((t.H + 7) / 8) * ((t.W + 7) / 8);
+            FeatImage &d = c.fb.img[i];
+            d.img = t.img;
+            d.ld = t.ld_img;
+            d.H = t.H;
+            d.W = t.W;
+            d.hist = cv.take<uint32_t>(256);
+            d.acc = cv.take<unsigned long long>(4);
+            d.dark = cv.take<uint8_t>(nb);
+            d.bmax = cv.take<uint8_t>(nb);
+        }
+        c.feat = cv.take<float>((size_t)cn * kNumFeatures);
+        c.picks = cv.take<int32_t>((size_t)cn);
+    }
+    c.fill.n = 0;
+    c.uf.n = 0;
+    c.eb.n = 0;
+    int fill_tiles = 0;
+    for (int i = 0; i < cn; ++i) {
+        const rt_tile &t = tiles[c0 + i];
+        const int H = t.H, W = t.W;
+        ReconImage &d = c.b.img[i];
+        // B = (R < threshold); F replaces it in place unless the caller wants F
+        uint8_t *B = cv.take<uint8_t>((size_t)H * W);
+        d.out = t.recon;
+        d.ld_out = t.ld_recon;
+        d.bin = B;
+        d.ld_bin = W;
+        uint8_t *F = t.filled ? t.filled : B;
+        const int64_t ldF = t.filled ? t.ld_filled : W;
+        char *fws = cv.take<char>(fill_image_bytes(H, W));
+        if (real) fill_add(c.fill, B, W, F, ldF, H, W, fws);
+        fill_tiles += (int)(ceil_div(H, kFillTH) * ceil_div(W, kFillTW));
+        char *uws = cv.take<char>(uf_workspace_bytes(H, W));
+        uint32_t *kept = cv.take<uint32_t>((size_t)H * ceil_div(W, 32));
+        char *ews = cv.take<char>(edt_bits_workspace_bytes(H, W));
+        if (real) {
+            UfImage u;
+            std::memset(&u, 0, sizeof(u));
+            uf_carve(u, uws, H, W);
+            u.in = F;
+            u.ld_in = ldF;
+            u.labels = t.labels;
+            u.ld_lab = t.ld_labels;
+            u.n_kept = t.n_kept;
+            u.fgbits = kept;
+            uf_add(c.uf, u);
+            edt_bits_add(c.eb, kept, H, W, t.d2, t.ld_d2, ews);
+        }
+    }
+    c.fill_flags = cv.take<uint32_t>((size_t)fill_tiles);
+    c.fill_pending = cv.take<uint32_t>(1);
+    c.uf.amin = P.min_area;
+    c.uf.amax = P.max_area;
+}
+
+// Workspace bytes rt_segment_batch needs for these tiles (the largest chunk).
+size_t segment_ws_bytes(const rt_tile *tiles, int n, const rt_seg_params &P, bool learned)
+{
+    size_t most = 0;
+    for (int c0 = 0; c0 < n; c0 += kMaxImgs) {
+        const int cn = n - c0 < kMaxImgs ? n - c0 : kMaxImgs;
+        Carve cv;
+        Chunk c;
+        layout_chunk(cv, c, tiles, c0, cn, P, learned);
+        most = cv.off > most ? cv.off : most;
+    }
+    return most;
 }
 
 }  // namespace
@@ -262,7 +388,7 @@ __global__ void copy_status_kernel(const int32_t *src, int32_t *dst)
 // ================================================================= C ABI
 extern "C" {
 
-int rt_version(void) { return 100; }
+int rt_version(void) { return 200; }
 
 const char *rt_status_str(int status)
 {
@@ -280,7 +406,7 @@ const char *rt_status_str(int status)
     }
 }
 
-rt_status rt_create(rt_ctx **ctx, int device)
+rt_status rt_create(rt_ctx **ctx, int device, size_t workspace_bytes)
 {
     if (!ctx) return RT_EINVAL;
     *ctx = nullptr;
@@ -301,8 +427,30 @@ rt_status rt_create(rt_ctx **ctx, int device)
         delete c;
         return RT_ECUDA;
     }
+    if (workspace_bytes > 0 && ensure_ws(c, workspace_bytes) != RT_OK) {
+        cudaEventDestroy(c->picks_ev);
+        cudaFreeHost(c->picks_host);
+        delete c;
+        return RT_ENOMEM;
+    }
     *ctx = c;
     return RT_OK;
+}
+
+rt_status rt_set_limits(rt_ctx *ctx, int max_iters, int timeout_ms)
+{
+    if (!ctx || max_iters < 0 || timeout_ms < 0) return RT_EINVAL;
+    ctx->max_iters = max_iters;
+    ctx->timeout_ns = (uint64_t)timeout_ms * 1000000ull;
+    return RT_OK;
+}
+
+size_t rt_segment_workspace_bytes(const rt_tile *tiles, int n, const rt_seg_params *params)
+{
+    if ((!tiles && n > 0) || n < 0 || !params || bad_params(*params)) return 0;
+    for (int i = 0; i < n; ++i)
+        if (bad_tile(tiles[i])) return 0;
+    return segment_ws_bytes(tiles, n, *params, params->policy == RT_POLICY_LEARNED);
 }
 
 void rt_destroy(rt_ctx *ctx)
@@ -423,11 +571,13 @@ rt_status rt_reconstruct(rt_ctx *ctx, const uint8_t *marker, int64_t ld_marker, 
 
     int32_t *err = dev_status ? dev_status : w.err;
     RT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
-    st = run_recon(ctx, b, w, conn, variant, 0, err, s);
+    st = run_recon(ctx, b, w, conn, variant, 0, err, s, ctx_limits(ctx));
     if (st != RT_OK) return st;
+    b.img[0].out = out;
+    b.img[0].ld_out = ld_out;
     Phase ph(ctx, RT_PHASE_RECON_OUT, s);
     ctx->launches += 1;
-    return cuda_status(launch_recon_out(b.img[0].Rw, b.img[0].Wp, out, ld_out, H, W, nullptr, 0, 0, s));
+    return cuda_status(launch_recon_out(b, 0, s));
 }
 
 rt_status rt_fill_holes(rt_ctx *ctx, const uint8_t *in, int64_t ld_in, uint8_t *out, int64_t ld_out, int H, int W,
@@ -464,7 +614,7 @@ rt_status rt_fill_holes(rt_ctx *ctx, const uint8_t *in, int64_t ld_in, uint8_t *
     fb.flags = flags;
     fb.pending = pend;
     fb.err = dev_status ? dev_status : err;
-    fb.timeout_ns = kSweepTimeoutNs;
+    fb.timeout_ns = ctx_limits(ctx).timeout_ns;
     Phase ph(ctx, RT_PHASE_FILL, s);
     ctx->launches += 3;
     return cuda_status(launch_fill(fb, ctx->num_sms, s));
@@ -479,24 +629,25 @@ rt_status rt_label_area(rt_ctx *ctx, const uint8_t *bin, int64_t ld_bin, int32_t
     if (overlaps(bin, span(H, ld_bin, 1, W), labels, span(H, ld_lab, 4, W))) return RT_EINVAL;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    UfArgs a;
-    Carve cv;
-    carve_uf(cv, a, H, W);
-    rt_status st = ensure_ws(ctx, cv.off);
+    rt_status st = ensure_ws(ctx, uf_workspace_bytes(H, W));
     if (st != RT_OK) return st;
-    cv = Carve();
-    cv.base = (char *)ctx->ws;
-    carve_uf(cv, a, H, W);
-    a.in = bin;
-    a.ld_in = ld_bin;
-    a.H = H;
-    a.W = W;
+    UfImage u;
+    std::memset(&u, 0, sizeof(u));
+    uf_carve(u, (char *)ctx->ws, H, W);
+    u.in = bin;
+    u.ld_in = ld_bin;
+    u.labels = labels;
+    u.ld_lab = ld_lab;
+    u.n_kept = dev_n_kept;
+    UfBatch b;
+    b.n = 0;
+    uf_add(b, u);
+    b.amin = min_area;
+    b.amax = max_area;
     if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
-    if (dev_n_kept) RT_CUDA_TRY(cudaMemsetAsync(dev_n_kept, 0, sizeof(int32_t), s));
     Phase ph(ctx, RT_PHASE_LABEL, s);
     ctx->launches += 4;
-    RT_CUDA_TRY(uf_build(a, conn, kFgNonzero, true, false, s));
-    return cuda_status(uf_labels_out(a, conn, labels, ld_lab, min_area, max_area, dev_n_kept, nullptr, s));
+    return cuda_status(launch_label_batch(b, conn, s));
 }
 
 rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int64_t ld_d2, int H, int W,
@@ -515,14 +666,12 @@ rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int
     EdtArgs a;
     a.fg8 = fg;
     a.lab32 = nullptr;
-    a.bits = nullptr;
     a.ld_in = ld_fg;
     a.H = H;
     a.W = W;
     a.d2 = d2;
     a.ld_d2 = ld_d2;
     a.g = cv.take<uint16_t>((size_t)H * W);
-    a.cmask = nullptr;
     a.seg = cv.take<int32_t>((size_t)2 * ceil_div(H, 32) * W);
     a.any_bg = cv.take<uint32_t>(1);
     if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
@@ -615,6 +764,14 @@ rt_status rt_mlp_backward(rt_ctx *ctx, const uint16_t *wb, const float *norm, co
                                            (cudaStream_t)stream));
 }
 
+rt_status rt_feature_norm(rt_ctx *ctx, const float *x, int B, float *norm, void *stream)
+{
+    if (!ctx || !x || !norm || B < 1) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    ctx->launches += 1;
+    return cuda_status(launch_feature_norm(x, B, norm, (cudaStream_t)stream));
+}
+
 rt_status rt_mlp_adamw(rt_ctx *ctx, float *master, uint16_t *wb, const float *grad, float *m, float *v, int step,
                        float lr, float beta1, float beta2, float eps, float weight_decay, void *stream)
 {
@@ -663,193 +820,91 @@ void rt_seg_params_default(rt_seg_params *p)
     p->variant = RT_AUTO;
     p->max_local = 0;
     p->policy = RT_POLICY_PLAIN;
+    p->max_iters = 0;
+    p->timeout_ms = 0;
 }
 
 rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_seg_params *params, void *stream)
 {
     if (!ctx || (!tiles && n > 0) || n < 0 || !params) return RT_EINVAL;
     const rt_seg_params &P = *params;
-    if (P.conn_recon != 4 && P.conn_recon != 8) return RT_EINVAL;
-    if (P.conn_fill != 4 && P.conn_fill != 8) return RT_EINVAL;
-    if (P.h_offset < 0 || P.h_offset > 255 || P.threshold < 0 || P.threshold > 256) return RT_EINVAL;
-    if (P.variant < RT_AUTO || P.variant > RT_HYBRID) return RT_EINVAL;
-    if (P.policy != RT_POLICY_PLAIN && P.policy != RT_POLICY_LEARNED) return RT_EINVAL;
-    int64_t maxN = 0;
-    for (int i = 0; i < n; ++i) {
-        const rt_tile &t = tiles[i];
-        if (!t.img || !t.labels || !t.d2 || bad_dims(t.H, t.W)) return RT_EINVAL;
-        if (t.ld_img < t.W || t.ld_labels < t.W || t.ld_d2 < t.W) return RT_EINVAL;
-        if (t.recon && t.ld_recon < t.W) return RT_EINVAL;
-        if (t.filled && t.ld_filled < t.W) return RT_EINVAL;
-        if ((int64_t)t.H * t.W > maxN) maxN = (int64_t)t.H * t.W;
-    }
+    if (bad_params(P)) return RT_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (bad_tile(tiles[i])) return RT_EINVAL;
     if (n == 0) return RT_OK;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    const bool learned = P.policy == RT_POLICY_LEARNED && ctx->picker_wb && ctx->picker_norm;
+    Limits lim = ctx_limits(ctx);
+    if (P.max_iters > 0) lim.max_iters = P.max_iters;
+    if (P.timeout_ms > 0) lim.timeout_ns = (uint64_t)P.timeout_ms * 1000000ull;
+    // one allocation for the largest chunk, before anything is enqueued
+    rt_status st = ensure_ws(ctx, segment_ws_bytes(tiles, n, P, learned));
+    if (st != RT_OK) return st;
 
     for (int c0 = 0; c0 < n; c0 += kMaxImgs) {
         const int cn = n - c0 < kMaxImgs ? n - c0 : kMaxImgs;
-        ReconBatch b;
-        std::memset(&b, 0, sizeof(b));
-        for (int i = 0; i < cn; ++i) {
-            const rt_tile &t = tiles[c0 + i];
-            add_image(b, nullptr, 0, t.img, t.ld_img, t.H, t.W, P.h_offset);
-        }
-        // workspace: recon buffers for the chunk, binary B per tile, then one
-        // shared set of union-find / EDT buffers (tiles run one after another)
-        int maxH = 0, maxW = 0;
-        for (int i = 0; i < cn; ++i) {
-            maxH = b.img[i].H > maxH ? b.img[i].H : maxH;
-            maxW = b.img[i].W > maxW ? b.img[i].W : maxW;
-        }
-        const bool learned = P.policy == RT_POLICY_LEARNED && ctx->picker_wb && ctx->picker_norm;
-        FeatBatch fb;
-        float *feat = nullptr;
-        int32_t *picks_dev = nullptr;
-        std::vector<char *> fill_ws;
-        uint32_t *fill_flags = nullptr, *fill_pending = nullptr;
-        uint32_t *kept_bits = nullptr;   // kept pixels of the tile being labeled, for its distance transform
-        auto layout = [&](Carve &cv, ReconWs &w, std::vector<uint8_t *> &Bs, char *&uf_ws,
-                          char *&edt_ws) {
-            carve_recon(cv, b, w, learned);
-            if (learned) {
-                fb.n = cn;
-                for (int i = 0; i < cn; ++i) {
-                    const rt_tile &t = tiles[c0 + i];
-                    const size_t nb = (size_t)((t.H + 7) / 8) * ((t.W + 7) / 8);
-                    FeatImage &d = fb.img[i];
-                    d.img = t.img;
-                    d.ld = t.ld_img;
-                    d.H = t.H;
-                    d.W = t.W;
-                    d.hist = cv.take<uint32_t>(256);
-                    d.acc = cv.take<unsigned long long>(4);
-                    d.dark = cv.take<uint8_t>(nb);
-                    d.bmax = cv.take<uint8_t>(nb);
-                }
-                feat = cv.take<float>((size_t)cn * kNumFeatures);
-                picks_dev = cv.take<int32_t>((size_t)cn);
-            }
-            Bs.resize(cn);
-            for (int i = 0; i < cn; ++i) Bs[i] = cv.take<uint8_t>((size_t)b.img[i].H * b.img[i].W);
-            // union-find pieces sized for (maxH, maxW), enough for every tile of the chunk
-            uf_ws = cv.take<char>(uf_workspace_bytes(maxH, maxW));
-            edt_ws = cv.take<char>(edt_workspace_bytes(maxH, maxW) + (size_t)maxN * 2);
-            fill_ws.resize(cn);
-            int fill_tiles = 0;
-            for (int i = 0; i < cn; ++i) {
-                fill_ws[i] = cv.take<char>(fill_image_bytes(b.img[i].H, b.img[i].W));
-                fill_tiles += (int)(ceil_div(b.img[i].H, kFillTH) * ceil_div(b.img[i].W, kFillTW));
-            }
-            fill_flags = cv.take<uint32_t>((size_t)fill_tiles);
-            kept_bits = cv.take<uint32_t>((size_t)maxH * ceil_div(maxW, 32));
-            fill_pending = cv.take<uint32_t>(1);
-        };
+        Chunk c;
         Carve cv;
-        ReconWs w;
-        std::vector<uint8_t *> Bs;
-        char *uf_ws, *edt_ws;
-        layout(cv, w, Bs, uf_ws, edt_ws);
-        rt_status st = ensure_ws(ctx, cv.off);
-        if (st != RT_OK) return st;
-        cv = Carve();
         cv.base = (char *)ctx->ws;
-        layout(cv, w, Bs, uf_ws, edt_ws);
-
-        RT_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int32_t), s));
+        layout_chunk(cv, c, tiles, c0, cn, P, learned);
+        RT_CUDA_TRY(cudaMemsetAsync(c.w.err, 0, sizeof(int32_t), s));
         if (!learned) {
-            st = run_recon(ctx, b, w, P.conn_recon, P.variant, P.max_local, w.err, s);
+            st = run_recon(ctx, c.b, c.w, P.conn_recon, P.variant, P.max_local, c.w.err, s, lim);
             if (st != RT_OK) return st;
         } else {
             // the picker chooses a variant per tile on the device; the
             // propagation reads its choices directly (no host round trip)
             {
                 Phase ph(ctx, RT_PHASE_PICK, s);
-                RT_CUDA_TRY(launch_features(fb, feat, s));
-                RT_CUDA_TRY(launch_mlp_forward(ctx->picker_wb, ctx->picker_norm, feat, cn, nullptr, nullptr,
-                                               picks_dev, s));
+                RT_CUDA_TRY(launch_features(c.fb, c.feat, s));
+                RT_CUDA_TRY(launch_mlp_forward(ctx->picker_wb, ctx->picker_norm, c.feat, cn, nullptr, nullptr, c.picks, s));
                 ctx->launches += 5;
             }
-            st = run_recon(ctx, b, w, P.conn_recon, P.variant, P.max_local, w.err, s, picks_dev);
+            st = run_recon(ctx, c.b, c.w, P.conn_recon, P.variant, P.max_local, c.w.err, s, lim, c.picks);
             if (st != RT_OK) return st;
-            RT_CUDA_TRY(cudaMemcpyAsync(ctx->picks_host, picks_dev, sizeof(int32_t) * cn, cudaMemcpyDeviceToHost, s));
+            RT_CUDA_TRY(cudaMemcpyAsync(ctx->picks_host, c.picks, sizeof(int32_t) * cn, cudaMemcpyDeviceToHost, s));
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusActive;
             if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cudaGetLastError();
             ctx->picks_ev_valid = cap == cudaStreamCaptureStatusNone;
             if (ctx->picks_ev_valid) RT_CUDA_TRY(cudaEventRecord(ctx->picks_ev, s));
             ctx->n_last_picks = cn;
         }
-        for (int i = 0; i < cn; ++i) {
-            const rt_tile &t = tiles[c0 + i];
-            const ReconImage &d = b.img[i];
+        {
             Phase ph(ctx, RT_PHASE_RECON_OUT, s);
             ctx->launches += 1;
-            RT_CUDA_TRY(launch_recon_out(d.Rw, d.Wp, t.recon, t.ld_recon, t.H, t.W, Bs[i], t.W, P.threshold, s));
+            RT_CUDA_TRY(launch_recon_out(c.b, P.threshold, s));
         }
-        // hole filling for the whole chunk at once; F replaces the binary
-        // image unless the caller wants F in its own buffer
         {
-            FillBatch fb_;
-            fb_.n = 0;
-            for (int i = 0; i < cn; ++i) {
-                const rt_tile &t = tiles[c0 + i];
-                uint8_t *F = t.filled ? t.filled : Bs[i];
-                fill_add(fb_, Bs[i], t.W, F, t.filled ? t.ld_filled : t.W, t.H, t.W, fill_ws[i]);
-            }
-            fb_.conn = P.conn_fill;
-            fb_.flags = fill_flags;
-            fb_.pending = fill_pending;
-            fb_.err = w.err;
-            fb_.timeout_ns = kSweepTimeoutNs;
+            c.fill.conn = P.conn_fill;
+            c.fill.flags = c.fill_flags;
+            c.fill.pending = c.fill_pending;
+            c.fill.err = c.w.err;
+            c.fill.timeout_ns = lim.timeout_ns;
             Phase ph(ctx, RT_PHASE_FILL, s);
             ctx->launches += 3;
-            RT_CUDA_TRY(launch_fill(fb_, ctx->num_sms, s));
+            RT_CUDA_TRY(launch_fill(c.fill, ctx->num_sms, s));
         }
+        {
+            Phase ph(ctx, RT_PHASE_LABEL, s);
+            ctx->launches += 4;
+            RT_CUDA_TRY(launch_label_batch(c.uf, 8, s));
+        }
+        {
+            Phase ph(ctx, RT_PHASE_EDT, s);
+            ctx->launches += 3;
+            RT_CUDA_TRY(launch_edt_bits_batch(c.eb, s));
+        }
+        StatusOut so;
+        bool any_status = false;
         for (int i = 0; i < cn; ++i) {
-            const rt_tile &t = tiles[c0 + i];
-            const int H = t.H, W = t.W;
-            const uint8_t *F = t.filled ? t.filled : Bs[i];
-            const int64_t ldF = t.filled ? t.ld_filled : W;
-            UfArgs la;
-            Carve uc;
-            uc.base = uf_ws;
-            carve_uf(uc, la, H, W);
-            la.H = H;
-            la.W = W;
-            la.in = F;
-            la.ld_in = ldF;
-            if (t.n_kept) RT_CUDA_TRY(cudaMemsetAsync(t.n_kept, 0, sizeof(int32_t), s));
-            {
-                Phase ph(ctx, RT_PHASE_LABEL, s);
-                ctx->launches += 4;
-                RT_CUDA_TRY(uf_build(la, 8, kFgNonzero, true, false, s));
-                RT_CUDA_TRY(uf_labels_out(la, 8, t.labels, t.ld_labels, P.min_area, P.max_area, t.n_kept, kept_bits, s));
-            }
-            EdtArgs ea;
-            ea.fg8 = nullptr;
-            ea.lab32 = nullptr;
-            ea.bits = kept_bits;
-            ea.ld_in = t.ld_labels;
-            ea.H = H;
-            ea.W = W;
-            ea.d2 = t.d2;
-            ea.ld_d2 = t.ld_d2;
-            Carve ec;
-            ec.base = edt_ws;
-            ea.g = nullptr;   // the bit-plane path computes g while staging each row
-            ea.cmask = ec.take<uint32_t>((size_t)ceil_div(H, 32) * W);
-            ea.seg = ec.take<int32_t>((size_t)2 * ceil_div(H, 32) * W);
-            ea.any_bg = ec.take<uint32_t>(1);
-            {
-                Phase ph(ctx, RT_PHASE_EDT, s);
-                ctx->launches += 3;
-                RT_CUDA_TRY(launch_edt(ea, s));
-            }
-            if (t.status) {
-                copy_status_kernel<<<1, 32, 0, s>>>(w.err, t.status);
-                ctx->launches += 1;
-                RT_CUDA_TRY(cudaGetLastError());
-            }
+            so.dst[i] = tiles[c0 + i].status;
+            any_status |= so.dst[i] != nullptr;
+        }
+        if (any_status) {
+            copy_status_kernel<<<1, 32, 0, s>>>(c.w.err, so, cn);
+            ctx->launches += 1;
+            RT_CUDA_TRY(cudaGetLastError());
         }
     }
     return RT_OK;

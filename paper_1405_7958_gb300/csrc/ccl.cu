@@ -8,17 +8,19 @@
 // the canonical label. The forest is built in two levels so that global
 // memory only ever holds the roots of block-local components:
 //   1. each 32 x 32 block labels its own pixels in shared memory; for every
-//      local root it records the local area (or whether the local component
-//      touches the image border) and appends the root to a list; for the
-//      pixels on the block's four edges it records their local root;
+//      local root it records the local area and lists the root in the
+//      block's own slots; for the pixels on the block's four edges it records
+//      their local root;
 //   2. local roots of pixels that touch across a block edge are merged in
 //      global memory (only those roots are nodes of the global forest);
 //   3. every listed local root is pointed at its final root, to which it adds
-//      its area (or its border-contact flag, for the components of the
-//      complement);
+//      its area;
 //   4. the output pass maps every pixel through its local root (recorded by
-//      pass 1) to its final root.
+//      pass 1) to its final root and applies the area filter.
+// Every stage is one launch over all the blocks of all the images of a batch
+// (a table of images; each CTA finds its image by the block numbering).
 #include "ccl.cuh"
+
 
 namespace rtk {
 
@@ -26,18 +28,70 @@ constexpr int kB = kUfBlock;
 constexpr int kRowsPerThread = 4;                     // warp w owns rows kRowsPerThread * w + 0, 1, ...
 constexpr int kThreads = 32 * kB / kRowsPerThread;    // threads per block CTA
 
+namespace {
+
+size_t piece(size_t bytes) { return (size_t)round_up((int64_t)bytes, 256); }
+
+}  // namespace
+
 size_t uf_workspace_bytes(int H, int W)
 {
     const size_t N = (size_t)H * W;
     const size_t nblk = (size_t)ceil_div(W, kB) * ceil_div(H, kB);
-    return 2 * N * sizeof(int32_t) + nblk * kUfEdge * sizeof(int32_t) + (N / 2 + 2) * sizeof(int32_t) +
-           N * sizeof(uint16_t) + nblk + 8 * 256;
+    return 2 * piece(N * sizeof(int32_t)) + piece(nblk * kUfEdge * sizeof(int32_t)) +
+           piece(nblk * kUfMaxRoots * sizeof(int32_t)) + piece(nblk * sizeof(uint16_t)) +
+           piece(N * sizeof(uint16_t)) + piece(nblk);
 }
 
-__device__ __forceinline__ bool is_fg(const uint8_t *in, int64_t ld, int r, int c, int source)
+void uf_carve(UfImage &d, char *base, int H, int W)
 {
-    const uint8_t v = in[(int64_t)r * ld + c];
-    return source == kFgNonzero ? v != 0 : v == 0;
+    const size_t N = (size_t)H * W;
+    d.H = H;
+    d.W = W;
+    d.nbx = (int)ceil_div(W, kB);
+    d.nby = (int)ceil_div(H, kB);
+    const size_t nblk = (size_t)d.nbx * d.nby;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base + off;
+        off += piece(bytes);
+        return p;
+    };
+    d.U = reinterpret_cast<int32_t *>(take(N * sizeof(int32_t)));
+    d.A = reinterpret_cast<int32_t *>(take(N * sizeof(int32_t)));
+    d.edge = reinterpret_cast<int32_t *>(take(nblk * kUfEdge * sizeof(int32_t)));
+    d.list = reinterpret_cast<int32_t *>(take(nblk * kUfMaxRoots * sizeof(int32_t)));
+    d.cnt = reinterpret_cast<uint16_t *>(take(nblk * sizeof(uint16_t)));
+    d.lroot = reinterpret_cast<uint16_t *>(take(N * sizeof(uint16_t)));
+    d.bempty = reinterpret_cast<uint8_t *>(take(nblk));
+}
+
+void uf_add(UfBatch &b, const UfImage &d)
+{
+    if (b.n == 0) b.nblk = 0;
+    UfImage &e = b.img[b.n++];
+    e = d;
+    e.blk_base = b.nblk;
+    b.nblk += (int64_t)d.nbx * d.nby;
+}
+
+// The image and block (bx, by) of CTA `g` of a launch over all blocks.
+struct BlockRef {
+    const UfImage *d;
+    int bx, by;
+    int64_t blk;   // block index inside the image
+};
+
+__device__ __forceinline__ BlockRef find_block(const UfBatch &b, int64_t g)
+{
+    int k = 0;
+    while (k + 1 < b.n && g >= b.img[k + 1].blk_base) ++k;
+    BlockRef r;
+    r.d = &b.img[k];
+    r.blk = g - r.d->blk_base;
+    r.bx = (int)(r.blk % r.d->nbx);
+    r.by = (int)(r.blk / r.d->nbx);
+    return r;
 }
 
 // --------------------------------------------------- shared-memory forest
@@ -118,8 +172,8 @@ __device__ __forceinline__ void union_g(int32_t *U, int32_t a, int32_t b)
 }
 
 // ---------------------------------------------------- block-local labeling
-// Labels block (blockIdx.x, blockIdx.y) in shared memory. Inside a row, a run
-// of foreground pixels is one tree from the start: every pixel points at the
+// Labels block (bx, by) of image d in shared memory. Inside a row, a run of
+// foreground pixels is one tree from the start: every pixel points at the
 // run's first pixel (found from the row's ballot mask). Rows are then joined
 // with one union per pair of touching runs: for 4-connectivity at the first
 // column where the runs overlap; for 8-connectivity the first pixel of a run
@@ -128,18 +182,18 @@ __device__ __forceinline__ void union_g(int32_t *U, int32_t a, int32_t b)
 // starts at its upper-right neighbour. On return roots[k] holds the local
 // index (lr * 32 + c) of the root of the thread's k-th pixel, or -1.
 template <int CONN>
-__device__ __forceinline__ bool local_labels(const UfArgs &a, int source, int *P, uint32_t *M,
+__device__ __forceinline__ bool local_labels(const UfImage &d, int bx, int by, int *P, uint32_t *M,
                                              int roots[kRowsPerThread])
 {
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
+    const int r0 = by * kB, c0 = bx * kB;
     const int c = c0 + tx;
     uint32_t any = 0;
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int lr = w * kRowsPerThread + k;
         const int r = r0 + lr;
-        const bool f = (r < a.H && c < a.W) && is_fg(a.in, a.ld_in, r, c, source);
+        const bool f = (r < d.H && c < d.W) && d.in[(int64_t)r * d.ld_in + c] != 0;
         const uint32_t m = __ballot_sync(0xffffffffu, f);
         const uint32_t starts = m & ~(m << 1);
         if (tx == 0) M[lr] = m;
@@ -186,71 +240,82 @@ __device__ __forceinline__ bool local_labels(const UfArgs &a, int source, int *P
     return true;
 }
 
-__device__ __forceinline__ int32_t global_index(const UfArgs &a, int local)
+__device__ __forceinline__ int32_t global_index(const UfImage &d, int bx, int by, int local)
 {
-    const int r = blockIdx.y * kB + local / kB, c = blockIdx.x * kB + local % kB;
-    return (int32_t)((int64_t)r * a.W + c);
+    const int r = by * kB + local / kB, c = bx * kB + local % kB;
+    return (int32_t)((int64_t)r * d.W + c);
 }
 
-// 1. block-local components, their roots, areas / border flags and edges
+// 1. block-local components, their roots, areas and edges. The first block
+// of an image also clears its kept-component count (read by stage 4).
 template <int CONN>
-__global__ void __launch_bounds__(kThreads) uf_local_kernel(UfArgs a, int source, bool count_area)
+__global__ void __launch_bounds__(kThreads) uf_local_kernel(UfBatch b)
 {
     __shared__ int P[kB * kB];
     __shared__ int cnt[kB * kB];
     __shared__ uint32_t M[kB];
+    __shared__ int nroots;
+    const BlockRef br = find_block(b, blockIdx.x);
+    const UfImage &d = *br.d;
+    const int bx = br.bx, by = br.by;
+    const int64_t blk = br.blk;
+    if (blk == 0 && threadIdx.x == 0 && d.n_kept) *d.n_kept = 0;
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     int roots[kRowsPerThread];
-    const bool nonempty = local_labels<CONN>(a, source, P, M, roots);
-    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB;
-    const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    int32_t *edge = a.edge + blk * kUfEdge;
-    if (!nonempty) {   // no roots, no edge roots; the output pass skips the block
+    const bool nonempty = local_labels<CONN>(d, bx, by, P, M, roots);
+    const int r0 = by * kB, c0 = bx * kB;
+    int32_t *edge = d.edge + blk * kUfEdge;
+    if (!nonempty) {   // no roots, no edge roots; the later stages skip the block
         if (threadIdx.x < kUfEdge) edge[threadIdx.x] = -1;
-        if (threadIdx.x == 0) a.bempty[blk] = 1;
+        if (threadIdx.x == 0) {
+            d.bempty[blk] = 1;
+            d.cnt[blk] = 0;
+        }
         return;
     }
-    if (threadIdx.x == 0) a.bempty[blk] = 0;
+    if (threadIdx.x == 0) {
+        d.bempty[blk] = 0;
+        nroots = 0;
+    }
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) cnt[(w * kRowsPerThread + k) * kB + tx] = 0;
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kRowsPerThread; ++k) {
-        if (roots[k] < 0) continue;
-        const int r = r0 + w * kRowsPerThread + k, c = c0 + tx;
-        if (count_area) atomicAdd(cnt + roots[k], 1);
-        else if (r == 0 || c == 0 || r == a.H - 1 || c == a.W - 1) cnt[roots[k]] = 1;
-    }
+    for (int k = 0; k < kRowsPerThread; ++k)
+        if (roots[k] >= 0) atomicAdd(cnt + roots[k], 1);
     __syncthreads();
     // every pixel's local root, so that the output pass need not label the block again
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int r = r0 + w * kRowsPerThread + k, c = c0 + tx;
-        if (r < a.H && c < a.W) a.lroot[(int64_t)r * a.W + c] = roots[k] >= 0 ? (uint16_t)roots[k] : (uint16_t)0xFFFFu;
+        if (r < d.H && c < d.W) d.lroot[(int64_t)r * d.W + c] = roots[k] >= 0 ? (uint16_t)roots[k] : (uint16_t)0xFFFFu;
     }
+    int32_t *list = d.list + blk * kUfMaxRoots;
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int lr = w * kRowsPerThread + k;
         const int i = lr * kB + tx;
-        const int32_t g = roots[k] >= 0 ? global_index(a, roots[k]) : -1;
+        const int32_t g = roots[k] >= 0 ? global_index(d, bx, by, roots[k]) : -1;
         if (lr == 0) edge[tx] = g;
         if (lr == kB - 1) edge[kB + tx] = g;
         if (tx == 0) edge[2 * kB + lr] = g;
         if (tx == kB - 1) edge[3 * kB + lr] = g;
         const bool is_root = roots[k] == i;
         if (is_root) {
-            a.U[g] = g;
-            a.A[g] = cnt[i];
+            d.U[g] = g;
+            d.A[g] = cnt[i];
         }
         const unsigned rm = __ballot_sync(0xffffffffu, is_root);
         if (rm) {
-            uint32_t base = 0;
+            int base = 0;
             const int leader = __ffs(rm) - 1;
-            if (tx == leader) base = atomicAdd(a.nlist, (uint32_t)__popc(rm));
+            if (tx == leader) base = atomicAdd(&nroots, __popc(rm));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (is_root) a.list[base + __popc(rm & ((1u << tx) - 1))] = g;
+            if (is_root) list[base + __popc(rm & ((1u << tx) - 1))] = g;
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) d.cnt[blk] = (uint16_t)nroots;
 }
 
 // 2. merges across block edges, one CTA of 96 threads per block: threads
@@ -261,11 +326,13 @@ __global__ void __launch_bounds__(kThreads) uf_local_kernel(UfArgs a, int source
 // along an edge only the first pixel pair of each pair of touching runs
 // needs a union; the others are skipped.
 template <int CONN>
-__global__ void __launch_bounds__(96) uf_border_kernel(UfArgs a)
+__global__ void __launch_bounds__(96) uf_border_kernel(UfBatch b)
 {
-    const int bx = blockIdx.x, by = blockIdx.y, nbx = gridDim.x;
+    const BlockRef br = find_block(b, blockIdx.x);
+    const UfImage &d = *br.d;
+    const int bx = br.bx, by = br.by, nbx = d.nbx;
     const int pos = threadIdx.x;
-    auto E = [&](int x, int y) -> const int32_t * { return a.edge + ((int64_t)y * nbx + x) * kUfEdge; };
+    auto E = [&](int x, int y) -> const int32_t * { return d.edge + ((int64_t)y * nbx + x) * kUfEdge; };
     const int32_t *me = E(bx, by);
     if (pos < 32) {
         if (by == 0) return;
@@ -275,12 +342,12 @@ __global__ void __launch_bounds__(96) uf_border_kernel(UfArgs a)
         const int32_t *ab = E(bx, by - 1) + kB;          // bottom row of the block above
         const bool left_in = k > 0 && me[k - 1] >= 0;
         const bool right_in = k < kB - 1 && me[k + 1] >= 0;
-        if (ab[k] >= 0 && !(left_in && ab[k - 1] >= 0)) union_g(a.U, p, ab[k]);
+        if (ab[k] >= 0 && !(left_in && ab[k - 1] >= 0)) union_g(d.U, p, ab[k]);
         if (CONN == 8) {
             const int32_t ul = k > 0 ? ab[k - 1] : (bx > 0 ? E(bx - 1, by - 1)[kB + kB - 1] : -1);
             const int32_t ur = k < kB - 1 ? ab[k + 1] : (bx + 1 < nbx ? E(bx + 1, by - 1)[kB] : -1);
-            if (ul >= 0 && !left_in) union_g(a.U, p, ul);
-            if (ur >= 0 && !right_in) union_g(a.U, p, ur);
+            if (ul >= 0 && !left_in) union_g(d.U, p, ul);
+            if (ur >= 0 && !right_in) union_g(d.U, p, ur);
         }
     } else if (pos < 64) {
         if (bx == 0) return;
@@ -289,8 +356,8 @@ __global__ void __launch_bounds__(96) uf_border_kernel(UfArgs a)
         if (p < 0) return;
         const int32_t *lr = E(bx - 1, by) + 3 * kB;      // right column of the block to the left
         const bool up_in = k > 0 && me[2 * kB + k - 1] >= 0;
-        if (lr[k] >= 0 && !(up_in && lr[k - 1] >= 0)) union_g(a.U, p, lr[k]);
-        if (CONN == 8 && k > 0 && lr[k - 1] >= 0 && !up_in) union_g(a.U, p, lr[k - 1]);
+        if (lr[k] >= 0 && !(up_in && lr[k - 1] >= 0)) union_g(d.U, p, lr[k]);
+        if (CONN == 8 && k > 0 && lr[k - 1] >= 0 && !up_in) union_g(d.U, p, lr[k - 1]);
     } else {
         if (CONN != 8 || bx + 1 >= nbx) return;
         const int k = pos - 64;
@@ -298,78 +365,77 @@ __global__ void __launch_bounds__(96) uf_border_kernel(UfArgs a)
         const int32_t p = me[3 * kB + k];
         if (p < 0) return;
         const int32_t q = E(bx + 1, by)[2 * kB + k - 1];  // left column of the block to the right, row above
-        if (q >= 0 && me[3 * kB + k - 1] < 0) union_g(a.U, p, q);
+        if (q >= 0 && me[3 * kB + k - 1] < 0) union_g(d.U, p, q);
     }
 }
 
-// 3. final roots of the local roots, with areas or border flags
-__global__ void uf_roots_kernel(UfArgs a, bool count_area)
+// 3. final roots of the local roots, with areas: a warp per block, lanes
+// over the block's listed roots (four blocks per CTA)
+__global__ void __launch_bounds__(128) uf_roots_kernel(UfBatch b)
 {
-    const uint32_t n = *a.nlist;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int32_t L = a.list[i];
-        const int32_t root = find_g_halve(a.U, L);
+    const int64_t g = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (g >= b.nblk) return;
+    const int lane = threadIdx.x & 31;
+    const BlockRef br = find_block(b, g);
+    const UfImage &d = *br.d;
+    const int n = d.cnt[br.blk];
+    const int32_t *list = d.list + br.blk * kUfMaxRoots;
+    for (int k = lane; k < n; k += 32) {
+        const int32_t L = list[k];
+        const int32_t root = find_g_halve(d.U, L);
         if (root == L) continue;
-        a.U[L] = root;     // plain store: no concurrent value can be smaller
-        if (count_area) atomicAdd(a.A + root, a.A[L]);
-        else if (a.A[L]) a.A[root] = 1;
+        d.U[L] = root;     // plain store: no concurrent value can be smaller
+        atomicAdd(d.A + root, d.A[L]);
     }
 }
 
-cudaError_t uf_build(const UfArgs &a, int conn, int source, bool count_area, bool flag_border, cudaStream_t s)
-{
-    (void)flag_border;
-    const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
-    cudaError_t e = cudaMemsetAsync(a.nlist, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    if (conn == 8) uf_local_kernel<8><<<grid_blk, kThreads, 0, s>>>(a, source, count_area);
-    else uf_local_kernel<4><<<grid_blk, kThreads, 0, s>>>(a, source, count_area);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (conn == 8) uf_border_kernel<8><<<grid_blk, 96, 0, s>>>(a);
-    else uf_border_kernel<4><<<grid_blk, 96, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    uf_roots_kernel<<<1024, 256, 0, s>>>(a, count_area);
-    return cudaGetLastError();
-}
-
-// 4a. labels with the area filter, from every pixel's local root (recorded
-// by pass 1); optionally the kept pixels as a bit plane (bit c % 32 of word
+// 4. labels with the area filter, from every pixel's local root (recorded
+// by stage 1); optionally the kept pixels as a bit plane (bit c % 32 of word
 // r * ceil(W / 32) + c / 32), which is all the distance transform needs
-__global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfArgs a, int32_t *labels, int64_t ld_lab, int32_t amin,
-                                                        int32_t amax, int32_t *n_kept, uint32_t *fgbits)
+__global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfBatch b)
 {
+    const BlockRef br = find_block(b, blockIdx.x);
+    const UfImage &d = *br.d;
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int r0 = blockIdx.y * kB, c0 = blockIdx.x * kB, c = c0 + tx;
-    const int64_t wpr = ceil_div(a.W, 32);
-    const bool empty = a.bempty[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] != 0;
+    const int r0 = br.by * kB, c0 = br.bx * kB, c = c0 + tx;
+    const int64_t wpr = ceil_div(d.W, 32);
+    const bool empty = d.bempty[br.blk] != 0;
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int r = r0 + w * kRowsPerThread + k;
-        const bool in = r < a.H && c < a.W;
-        const uint32_t lr = in && !empty ? a.lroot[(int64_t)r * a.W + c] : 0xFFFFu;
+        const bool in = r < d.H && c < d.W;
+        const uint32_t lr = in && !empty ? d.lroot[(int64_t)r * d.W + c] : 0xFFFFu;
         int32_t out = -1;
         if (lr != 0xFFFFu) {
-            const int32_t root = a.U[global_index(a, (int)lr)];
-            const int32_t area = a.A[root];
-            if (area >= amin && area <= amax) {
+            const int32_t root = d.U[global_index(d, br.bx, br.by, (int)lr)];
+            const int32_t area = d.A[root];
+            if (area >= b.amin && area <= b.amax) {
                 out = root;
-                if (n_kept && root == (int32_t)((int64_t)r * a.W + c)) atomicAdd(n_kept, 1);
+                if (d.n_kept && root == (int32_t)((int64_t)r * d.W + c)) atomicAdd(d.n_kept, 1);
             }
         }
-        if (in) labels[(int64_t)r * ld_lab + c] = out;
-        if (fgbits) {
+        if (in) d.labels[(int64_t)r * d.ld_lab + c] = out;
+        if (d.fgbits) {
             const uint32_t bits = __ballot_sync(0xffffffffu, out >= 0);
-            if (tx == 0 && r < a.H) fgbits[(int64_t)r * wpr + blockIdx.x] = bits;
+            if (tx == 0 && r < d.H) d.fgbits[(int64_t)r * wpr + br.bx] = bits;
         }
     }
 }
 
-cudaError_t uf_labels_out(const UfArgs &a, int conn, int32_t *labels, int64_t ld_lab, int32_t min_area,
-                          int32_t max_area, int32_t *n_kept, uint32_t *fgbits, cudaStream_t s)
+cudaError_t launch_label_batch(const UfBatch &b, int conn, cudaStream_t s)
 {
-    const dim3 grid_blk((unsigned)ceil_div(a.W, kB), (unsigned)ceil_div(a.H, kB));
-    (void)conn;   // the components were built by uf_build with this connectivity
-    uf_labels_kernel<<<grid_blk, kThreads, 0, s>>>(a, labels, ld_lab, min_area, max_area, n_kept, fgbits);
+    if (b.n < 1 || b.n > kUfMaxImgs || (conn != 4 && conn != 8)) return cudaErrorInvalidValue;
+    const unsigned nb = (unsigned)b.nblk;
+    if (conn == 8) uf_local_kernel<8><<<nb, kThreads, 0, s>>>(b);
+    else uf_local_kernel<4><<<nb, kThreads, 0, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (conn == 8) uf_border_kernel<8><<<nb, 96, 0, s>>>(b);
+    else uf_border_kernel<4><<<nb, 96, 0, s>>>(b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    uf_roots_kernel<<<(unsigned)ceil_div(b.nblk, 4), 128, 0, s>>>(b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    uf_labels_kernel<<<nb, kThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 

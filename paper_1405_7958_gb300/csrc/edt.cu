@@ -8,11 +8,12 @@
 // Vertical pass: columns are cut into 32-row segments; a first kernel
 // records each segment's first and last background row, a second one walks
 // every segment with the carries from the segments above and below.
-// With a bit-plane input g is never stored: a first kernel turns each 32 x 32
-// block's row words into column masks (ballots), a second records for every
-// segment and column the nearest background row above and below the
-// segment, and the horizontal pass computes the g values of its row from
-// those (bit scans of the column's mask) while staging them.
+// With a bit-plane input (the segmentation chain, a batch of images per
+// launch) g is never stored: a first kernel turns each 32 x 32 block's row
+// words into column masks (ballots), a second records for every segment and
+// column the nearest background row above and below the segment, and the
+// horizontal pass computes the g values of its row from those (bit scans of
+// the column's mask) while staging them.
 // Horizontal pass: a CTA per row stages g in shared memory. For pixel c the
 // candidate c' = c gives g(r,c)^2, and any c' with |c - c'| >= sqrt(best)
 // cannot win, so the search runs outward from c and stops as soon as
@@ -34,7 +35,6 @@ size_t edt_workspace_bytes(int H, int W)
 
 __device__ __forceinline__ bool edt_is_bg(const EdtArgs &a, int r, int c)
 {
-    if (a.bits) return !((a.bits[(int64_t)r * ceil_div(a.W, 32) + (c >> 5)] >> (c & 31)) & 1u);
     if (a.lab32) return a.lab32[(int64_t)r * a.ld_in + c] < 0;
     return a.fg8[(int64_t)r * a.ld_in + c] == 0;
 }
@@ -93,62 +93,10 @@ __global__ void edt_col_kernel(EdtArgs a)
     }
 }
 
-// Bit-plane input: a warp covers the 32 columns of one plane word and one
-// segment. Lane i loads the word of row rb + i; 32 ballots turn the rows'
-// words into the columns' masks, lane j getting column 32 * wc + j with bit
-// i set where row rb + i is background. Rows past the end count as
-// foreground.
-__device__ __forceinline__ uint32_t seg_bg_mask(const EdtArgs &a, int64_t wpr, int wc, int rb, int lane)
-{
-    const int r = rb + lane;
-    const uint32_t w = r < a.H ? __ldg(a.bits + (int64_t)r * wpr + wc) : 0xffffffffu;
-    uint32_t m = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const uint32_t b = __ballot_sync(0xffffffffu, !((w >> j) & 1u));
-        m = lane == j ? b : m;
-    }
-    return m;
-}
-
-// warp per (plane word column, segment): the segment's column masks
-__global__ void __launch_bounds__(128) edt_mask_bits_kernel(EdtArgs a)
-{
-    const int64_t wpr = ceil_div(a.W, 32);
-    const int wc = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (wc >= wpr) return;
-    const int s = blockIdx.y, rb = s * kSeg;
-    const uint32_t bg = seg_bg_mask(a, wpr, wc, rb, lane);
-    const int c = wc * 32 + lane;
-    if (c >= a.W) return;
-    a.cmask[(int64_t)s * a.W + c] = bg;
-    if (bg && *a.any_bg == 0) atomicOr(a.any_bg, 1u);
-}
-
-// thread per (column, segment): the last background row above the segment
-// and the first one below it (-1: none)
-__global__ void edt_chase_bits_kernel(EdtArgs a)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
-    if (c >= a.W) return;
-    const int nseg = (int)ceil_div(a.H, kSeg);
-    int above = -1;
-    for (int t = s - 1; t >= 0; --t) {
-        const uint32_t m = a.cmask[(int64_t)t * a.W + c];
-        if (m) { above = t * kSeg + 31 - __clz(m); break; }
-    }
-    int below = -1;
-    for (int t = s + 1; t < nseg; ++t) {
-        const uint32_t m = a.cmask[(int64_t)t * a.W + c];
-        if (m) { below = t * kSeg + __ffs(m) - 1; break; }
-    }
-    a.seg[(int64_t)s * a.W + c] = above;
-    a.seg[(int64_t)(nseg + s) * a.W + c] = below;
-}
-
 // d2 of one row from its g values in shared memory: for pixel c the search
-// runs outward from c and stops once (c - c')^2 reaches the best value
+// runs outward from c and stops once (c - c')^2 reaches the best value. A
+// pixel that finds no background in any column gets -1 (the image has no
+// background: a column with background gives every row a finite g there).
 __device__ __forceinline__ void edt_row_search(const uint16_t *sg, int W, bool any, int32_t *out)
 {
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
@@ -157,7 +105,8 @@ __device__ __forceinline__ void edt_row_search(const uint16_t *sg, int W, bool a
             continue;
         }
         const int gc = sg[c];
-        long long best = gc == kInf ? 0x7fffffffffffLL : (long long)gc * gc;
+        constexpr long long kNone = 0x7fffffffffffLL;
+        long long best = gc == kInf ? kNone : (long long)gc * gc;
         for (int d = 1; (long long)d * d < best; ++d) {
             const int cl = c - d, cr = c + d;
             if (cl < 0 && cr >= W) break;
@@ -176,7 +125,7 @@ __device__ __forceinline__ void edt_row_search(const uint16_t *sg, int W, bool a
                 }
             }
         }
-        out[c] = (int32_t)best;
+        out[c] = best == kNone ? -1 : (int32_t)best;
     }
 }
 
@@ -197,13 +146,141 @@ __global__ void edt_row_kernel(EdtArgs a)
     edt_row_search(sg, a.W, *a.any_bg != 0, a.d2 + (int64_t)r * a.ld_d2);
 }
 
-// CTA per row, bit-plane input: g of the row from the column masks of its
-// segment (and, where the segment has no background on one side of the row,
-// the nearest background beyond it), then the same search
-__global__ void edt_row_bits_kernel(EdtArgs a)
+cudaError_t launch_edt(const EdtArgs &a, cudaStream_t s)
+{
+    const int nseg = (int)ceil_div(a.H, kSeg);
+    cudaError_t e = cudaMemsetAsync(a.any_bg, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)a.W * sizeof(uint16_t);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(edt_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const dim3 g1((unsigned)ceil_div(a.W, 128), (unsigned)nseg);
+    edt_seg_kernel<<<g1, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    edt_col_kernel<<<g1, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    edt_row_kernel<<<(unsigned)a.H, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- bit-plane batch
+namespace {
+size_t piece(size_t bytes) { return (size_t)round_up((int64_t)bytes, 256); }
+}  // namespace
+
+size_t edt_bits_workspace_bytes(int H, int W)
+{
+    const size_t nseg = (size_t)ceil_div(H, kSeg);
+    return piece(nseg * W * sizeof(uint32_t)) + piece(2 * nseg * W * sizeof(int32_t));
+}
+
+constexpr int kMaskWarps = 4;   // plane word columns per CTA of the mask stage
+constexpr int kColThreads = 128;
+
+void edt_bits_add(EdtBitsBatch &b, const uint32_t *bits, int H, int W, int32_t *d2, int64_t ld_d2, char *base)
+{
+    if (b.n == 0) {
+        b.maxW = 0;
+        b.mask_ctas = b.col_ctas = b.rows = 0;
+    }
+    EdtBitsImage &d = b.img[b.n++];
+    const int64_t nseg = ceil_div(H, kSeg);
+    d.bits = bits;
+    d.H = H;
+    d.W = W;
+    d.d2 = d2;
+    d.ld_d2 = ld_d2;
+    d.cmask = reinterpret_cast<uint32_t *>(base);
+    d.seg = reinterpret_cast<int32_t *>(base + piece((size_t)nseg * W * sizeof(uint32_t)));
+    d.mask_base = b.mask_ctas;
+    d.col_base = b.col_ctas;
+    d.row_base = b.rows;
+    b.mask_ctas += ceil_div(ceil_div(W, 32), kMaskWarps) * nseg;
+    b.col_ctas += ceil_div(W, kColThreads) * nseg;
+    b.rows += H;
+    b.maxW = W > b.maxW ? W : b.maxW;
+}
+
+// the image whose CTA range [base, next base) holds CTA g of a stage
+template <int64_t EdtBitsImage::*BASE>
+__device__ __forceinline__ const EdtBitsImage &edt_image(const EdtBitsBatch &b, int64_t g)
+{
+    int k = 0;
+    while (k + 1 < b.n && g >= b.img[k + 1].*BASE) ++k;
+    return b.img[k];
+}
+
+// Lane i loads the plane word (32 columns starting at 32 * wc) of row
+// rb + i; 32 ballots turn the rows' words into the columns' masks, lane j
+// getting column 32 * wc + j with bit i set where row rb + i is background.
+// Rows past the end count as foreground.
+__device__ __forceinline__ uint32_t seg_bg_mask(const EdtBitsImage &a, int64_t wpr, int wc, int rb, int lane)
+{
+    const int r = rb + lane;
+    const uint32_t w = r < a.H ? __ldg(a.bits + (int64_t)r * wpr + wc) : 0xffffffffu;
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t b = __ballot_sync(0xffffffffu, !((w >> j) & 1u));
+        m = lane == j ? b : m;
+    }
+    return m;
+}
+
+// warp per (plane word column, segment): the segment's column masks
+__global__ void __launch_bounds__(kMaskWarps * 32) edt_mask_bits_kernel(EdtBitsBatch b)
+{
+    const EdtBitsImage &a = edt_image<&EdtBitsImage::mask_base>(b, blockIdx.x);
+    const int64_t wpr = ceil_div(a.W, 32);
+    const int64_t local = blockIdx.x - a.mask_base;
+    const int64_t gx = ceil_div(wpr, kMaskWarps);
+    const int s = (int)(local / gx);
+    const int wc = (int)(local % gx) * kMaskWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (wc >= wpr) return;
+    const int rb = s * kSeg;
+    const uint32_t bg = seg_bg_mask(a, wpr, wc, rb, lane);
+    const int c = wc * 32 + lane;
+    if (c >= a.W) return;
+    a.cmask[(int64_t)s * a.W + c] = bg;
+}
+
+// thread per (column, segment): the last background row above the segment
+// and the first one below it (-1: none)
+__global__ void __launch_bounds__(kColThreads) edt_chase_bits_kernel(EdtBitsBatch b)
+{
+    const EdtBitsImage &a = edt_image<&EdtBitsImage::col_base>(b, blockIdx.x);
+    const int64_t local = blockIdx.x - a.col_base;
+    const int64_t gx = ceil_div(a.W, kColThreads);
+    const int s = (int)(local / gx);
+    const int c = (int)(local % gx) * kColThreads + threadIdx.x;
+    if (c >= a.W) return;
+    const int nseg = (int)ceil_div(a.H, kSeg);
+    int above = -1;
+    for (int t = s - 1; t >= 0; --t) {
+        const uint32_t m = a.cmask[(int64_t)t * a.W + c];
+        if (m) { above = t * kSeg + 31 - __clz(m); break; }
+    }
+    int below = -1;
+    for (int t = s + 1; t < nseg; ++t) {
+        const uint32_t m = a.cmask[(int64_t)t * a.W + c];
+        if (m) { below = t * kSeg + __ffs(m) - 1; break; }
+    }
+    a.seg[(int64_t)s * a.W + c] = above;
+    a.seg[(int64_t)(nseg + s) * a.W + c] = below;
+}
+
+// CTA per row: g of the row from the column masks of its segment (and,
+// where the segment has no background on one side of the row, the nearest
+// background beyond it), then the search. A row that finds no background
+// anywhere belongs to an image without background (every column's g is
+// infinite then), whose distances are -1.
+__global__ void edt_row_bits_kernel(EdtBitsBatch b)
 {
     extern __shared__ uint16_t sg[];
-    const int r = blockIdx.x, s = r / kSeg, i = r % kSeg, rb = s * kSeg;
+    const EdtBitsImage &a = edt_image<&EdtBitsImage::row_base>(b, blockIdx.x);
+    const int r = (int)(blockIdx.x - a.row_base), s = r / kSeg, i = r % kSeg, rb = s * kSeg;
     const int nseg = (int)ceil_div(a.H, kSeg);
     const uint32_t *cm = a.cmask + (int64_t)s * a.W;
     // four columns per thread at a time: their mask loads are issued together
@@ -234,34 +311,23 @@ __global__ void edt_row_bits_kernel(EdtArgs a)
         }
     }
     __syncthreads();
-    edt_row_search(sg, a.W, *a.any_bg != 0, a.d2 + (int64_t)r * a.ld_d2);
+    edt_row_search(sg, a.W, true, a.d2 + (int64_t)r * a.ld_d2);
 }
 
-cudaError_t launch_edt(const EdtArgs &a, cudaStream_t s)
+cudaError_t launch_edt_bits_batch(const EdtBitsBatch &b, cudaStream_t s)
 {
-    const int nseg = (int)ceil_div(a.H, kSeg);
-    cudaError_t e = cudaMemsetAsync(a.any_bg, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)a.W * sizeof(uint16_t);
-    const void *row_fn = a.bits ? (const void *)edt_row_bits_kernel : (const void *)edt_row_kernel;
+    if (b.n < 1 || b.n > kEdtMaxImgs) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)b.maxW * sizeof(uint16_t);
+    cudaError_t e;
     if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(row_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(edt_row_bits_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    if (a.bits) {
-        edt_mask_bits_kernel<<<dim3((unsigned)ceil_div(ceil_div(a.W, 32), 4), (unsigned)nseg), 128, 0, s>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        edt_chase_bits_kernel<<<dim3((unsigned)ceil_div(a.W, 128), (unsigned)nseg), 128, 0, s>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        edt_row_bits_kernel<<<(unsigned)a.H, 256, smem, s>>>(a);
-    } else {
-        const dim3 g1((unsigned)ceil_div(a.W, 128), (unsigned)nseg);
-        edt_seg_kernel<<<g1, 128, 0, s>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        edt_col_kernel<<<g1, 128, 0, s>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        edt_row_kernel<<<(unsigned)a.H, 256, smem, s>>>(a);
-    }
+    edt_mask_bits_kernel<<<(unsigned)b.mask_ctas, kMaskWarps * 32, 0, s>>>(b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    edt_chase_bits_kernel<<<(unsigned)b.col_ctas, kColThreads, 0, s>>>(b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    edt_row_bits_kernel<<<(unsigned)b.rows, 256, smem, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -68,14 +68,12 @@ extern "C" rt_status rt_edt_noalloc(const uint8_t *fg, int64_t ld_fg, int32_t *d
     rtk::EdtArgs a;
     a.fg8 = fg;
     a.lab32 = nullptr;
-    a.bits = nullptr;
     a.ld_in = ld_fg;
     a.H = H;
     a.W = W;
     a.d2 = d2;
     a.ld_d2 = ld_d2;
     a.g = reinterpret_cast<uint16_t *>(base);
-    a.cmask = nullptr;
     a.seg = reinterpret_cast<int32_t *>(base + kDistBytes);
     a.any_bg = reinterpret_cast<uint32_t *>(base + kDistBytes + kSegBytes);   // cleared by launch_edt
     if (dev_status && cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s) != cudaSuccess) {

@@ -197,4 +197,49 @@ cudaError_t launch_mlp_adamw(float *master, uint16_t *wb, const float *grad, flo
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------- input normalisation
+// One CTA per feature column: each thread sums a fixed stride of rows in
+// double, then a fixed-shape tree adds the partial sums; two passes (mean,
+// then squared deviations).
+constexpr int kNormThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int k = kNormThreads / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kNormThreads) feature_norm_kernel(const float *x, int B, float *norm)
+{
+    __shared__ double sh[kNormThreads];
+    const int f = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < B; b += kNormThreads) s += (double)x[(int64_t)b * kMlpIn + f];
+    const double mean = block_sum(s, sh) / B;
+    double q = 0.0;
+    for (int b = threadIdx.x; b < B; b += kNormThreads) {
+        const double d = (double)x[(int64_t)b * kMlpIn + f] - mean;
+        q += d * d;
+    }
+    const double ss = block_sum(q, sh);
+    if (threadIdx.x == 0) {
+        const double sd = B > 1 ? sqrt(ss / (B - 1)) : 0.0;
+        norm[f] = (float)mean;
+        norm[kMlpIn + f] = (float)(sd > 1e-6 ? sd : 1e-6);
+    }
+}
+
+cudaError_t launch_feature_norm(const float *x, int B, float *norm, cudaStream_t s)
+{
+    feature_norm_kernel<<<kMlpIn, kNormThreads, 0, s>>>(x, B, norm);
+    return cudaGetLastError();
+}
+
 }  // namespace rtk

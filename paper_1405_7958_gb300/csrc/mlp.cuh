@@ -23,6 +23,10 @@ size_t mlp_backward_workspace_bytes(int B);
 cudaError_t launch_mlp_backward(const uint16_t *wb, const float *norm, const float *x, const float *act,
                                 const float *logits, const int32_t *label, int B, float *grad, float *loss, float *ws,
                                 cudaStream_t s);
+// norm = (mean[24], std[24]) of the columns of x (B x 24): the mean, and the
+// sample standard deviation (divisor B - 1; 0 for B = 1) clamped below at
+// 1e-6; sums in double in a fixed order (deterministic)
+cudaError_t launch_feature_norm(const float *x, int B, float *norm, cudaStream_t s);
 cudaError_t launch_mlp_adamw(float *master, uint16_t *wb, const float *grad, float *m, float *v, int step, float lr,
                              float b1, float b2, float eps, float wd, cudaStream_t s);
 

@@ -667,9 +667,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
     const uint64_t t_start = globaltimer_ns();
     uint32_t nvisits = 0, work = 0;
     int idle = 0;
+    bool stop = false;
     for (;;) {
         bool did = false;
-        for (int base = own0; base < own1; base += 32) {
+        for (int base = own0; base < own1 && !stop; base += 32) {
             const int vl = base + lane;
             const int tl = vl < own1 ? (p.map ? p.map[vl] : vl) : 0;
             const bool f = vl < own1 && *reinterpret_cast<volatile uint32_t *>(p.flags + tl) != 0u;
@@ -679,8 +680,25 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
                 mask &= mask - 1;
                 const int t = __shfl_sync(0xffffffffu, tl, i);
                 uint32_t got = 0;
-                if (lane == 0) got = atomicExch(p.flags + t, 0u);
+                if (lane == 0) {
+                    // a visit starts only within the visit bound and before
+                    // any bound was reached; past one the propagation stops
+                    // short of the fixed point and says so
+                    if (*reinterpret_cast<volatile uint32_t *>(p.abort)) {
+                        got = 0xffffffffu;
+                    } else if (p.max_visits && atomicAdd(p.spent, 1u) >= p.max_visits) {
+                        raise_status(p.err, RT_ETIMEOUT);
+                        atomicExch(p.abort, 1u);
+                        got = 0xffffffffu;
+                    } else {
+                        got = atomicExch(p.flags + t, 0u);
+                    }
+                }
                 got = __shfl_sync(0xffffffffu, got, 0);
+                if (got == 0xffffffffu) {
+                    stop = true;
+                    break;
+                }
                 if (!got) continue;
                 __threadfence();
                 if (QUEUE) work += visit_queue<CONN>(p, t, got, qb, lane);
@@ -690,19 +708,23 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
                 ++nvisits;
             }
         }
+        if (stop) break;
         if (did) {
             idle = 0;
             continue;
         }
         uint32_t pend = 0;
-        if (lane == 0) pend = ld_acquire(p.pending);
+        if (lane == 0) pend = ld_acquire(p.abort) ? 0u : ld_acquire(p.pending);
         pend = __shfl_sync(0xffffffffu, pend, 0);
         if (pend == 0) break;
         if (++idle > 4) __nanosleep(1500);
         int late = 0;
         if (lane == 0 && (idle & 63) == 0) late = globaltimer_ns() - t_start > p.timeout_ns;
         if (__shfl_sync(0xffffffffu, late, 0)) {
-            if (lane == 0) raise_status(p.err, RT_ETIMEOUT);
+            if (lane == 0) {
+                raise_status(p.err, RT_ETIMEOUT);
+                atomicExch(p.abort, 1u);
+            }
             break;
         }
     }
@@ -750,18 +772,18 @@ cudaError_t launch_recon_persistent(const SweepParams &p, int conn, int queue, i
 }
 
 // --------------------------------------------------------------- output
-// out = R (cropped to H x W); optionally bin = (R < threshold). One row per
-// blockIdx.y, 16 columns per thread.
-__global__ void recon_out_kernel(const uint8_t *Rw, int Wp, uint8_t *out, int64_t ld_out, int H, int W,
-                                 uint8_t *bin, int64_t ld_bin, int threshold)
+// out = R (cropped to H x W) and bin = (R < threshold), either optional,
+// for image blockIdx.z; one row per blockIdx.y, 16 columns per thread.
+__global__ void recon_out_kernel(const ReconBatch b, int threshold)
 {
+    const ReconImage &d = b.img[blockIdx.z];
     const int r = blockIdx.y;
     const int c0 = (blockIdx.x * blockDim.x + threadIdx.x) * 16;
-    if (c0 >= W) return;
-    const int n = min(16, W - c0);
-    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(Rw + (int64_t)r * Wp + c0));
-    if (out) store16(out + (int64_t)r * ld_out + c0, v, n);
-    if (bin) {
+    if (r >= d.H || c0 >= d.W) return;
+    const int n = min(16, d.W - c0);
+    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(d.Rw + (int64_t)r * d.Wp + c0));
+    if (d.out) store16(d.out + (int64_t)r * d.ld_out + c0, v, n);
+    if (d.bin) {
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
         uint32_t o[4];
 #pragma unroll
@@ -771,16 +793,20 @@ __global__ void recon_out_kernel(const uint8_t *Rw, int Wp, uint8_t *out, int64_
             for (int k = 0; k < 4; ++k) x |= (uint32_t)((int)((w[q] >> (8 * k)) & 0xffu) < threshold) << (8 * k);
             o[q] = x;
         }
-        store16(bin + (int64_t)r * ld_bin + c0, make_uint4(o[0], o[1], o[2], o[3]), n);
+        store16(d.bin + (int64_t)r * d.ld_bin + c0, make_uint4(o[0], o[1], o[2], o[3]), n);
     }
 }
 
-cudaError_t launch_recon_out(const uint8_t *Rw, int Wp, uint8_t *out, int64_t ld_out, int H, int W,
-                             uint8_t *bin, int64_t ld_bin, int threshold, cudaStream_t s)
+cudaError_t launch_recon_out(const ReconBatch &b, int threshold, cudaStream_t s)
 {
+    int maxH = 1, maxW = 1;
+    for (int i = 0; i < b.n; ++i) {
+        maxH = b.img[i].H > maxH ? b.img[i].H : maxH;
+        maxW = b.img[i].W > maxW ? b.img[i].W : maxW;
+    }
     const int threads = 128;
-    recon_out_kernel<<<dim3((unsigned)ceil_div(ceil_div(W, 16), threads), (unsigned)H), threads, 0, s>>>(
-        Rw, Wp, out, ld_out, H, W, bin, ld_bin, threshold);
+    recon_out_kernel<<<dim3((unsigned)ceil_div(ceil_div(maxW, 16), threads), (unsigned)maxH, (unsigned)b.n), threads, 0,
+                       s>>>(b, threshold);
     return cudaGetLastError();
 }
 

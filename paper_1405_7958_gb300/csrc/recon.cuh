@@ -29,6 +29,10 @@ struct ReconImage {
     int tiles_x, tiles_y;
     int tile_base;          // index of this image's first tile in the batch
     int h_offset;
+    uint8_t *out;           // nullable: R, H x W, stride ld_out (output pass)
+    int64_t ld_out;
+    uint8_t *bin;           // nullable: B = (R < threshold), H x W, stride ld_bin (output pass)
+    int64_t ld_bin;
 };
 
 constexpr int kMaxImgs = 32;
@@ -49,7 +53,10 @@ struct SweepParams {
     int32_t *err;             // device status word
     uint32_t *visits;         // [0] tile visits, [1] dense iterations, [2] queue pops (statistics)
     int max_local;            // local iterations per visit before revisiting
-    uint64_t timeout_ns;      // bound on the whole propagation
+    uint64_t timeout_ns;      // bound on the whole propagation (device time)
+    uint32_t max_visits;      // bound on the tile visits of the propagation (0 = none)
+    uint32_t *spent;          // visits started so far (device word, zeroed with the control words)
+    uint32_t *abort;          // nonzero: a bound was reached, every warp leaves
     const int32_t *map;       // NULL: the launch covers tiles 0..ntiles-1; else its k-th tile is map[k]
     const uint32_t *nvirt;    // with map: number of tiles the launch covers (device word)
 };
@@ -62,6 +69,8 @@ constexpr int kCtlPending = 0;
 constexpr int kCtlVisits = 1;
 constexpr int kCtlGroupPending = 4;
 constexpr int kCtlGroupCount = 8;
+constexpr int kCtlSpent = 12;
+constexpr int kCtlAbort = 13;
 constexpr int kCtlWords = 16;
 constexpr int kGroups = 3;    // RT_RASTER, RT_QUEUE, RT_HYBRID
 
@@ -80,7 +89,8 @@ cudaError_t launch_recon_dense(const SweepParams &p, int conn, cudaStream_t s);
 // persistent visits of flagged tiles until quiescence; queue = 1: queue visits
 cudaError_t launch_recon_persistent(const SweepParams &p, int conn, int queue, int num_sms, cudaStream_t s,
                                     int *grid_used);
-cudaError_t launch_recon_out(const uint8_t *Rw, int Wp, uint8_t *out, int64_t ld_out, int H, int W,
-                             uint8_t *bin, int64_t ld_bin, int threshold, cudaStream_t s);
+// R and B = (R < threshold) of every image of the batch into its out / bin
+// (either may be NULL), one launch
+cudaError_t launch_recon_out(const ReconBatch &b, int threshold, cudaStream_t s);
 
 }  // namespace rtk

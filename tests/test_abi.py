@@ -36,7 +36,7 @@ def test_binding_lists_every_export(built):
     from paper_1405_7958_gb300 import _native
     assert sorted(_native.EXPORTS) == declared_symbols()
     lib = _native.load(built)
-    assert lib.rt_version() == 100
+    assert lib.rt_version() == 200
     assert lib.rt_status_str(4).decode().startswith("RT_ETIMEOUT")
 
 
@@ -48,4 +48,40 @@ def test_argument_validation_without_gpu(built):
     # NULL context
     assert lib.rt_reconstruct(None, None, 0, bogus, 8, bogus, 8, 4, 4, 8, 0, 30, None, None) == _native.RT_EINVAL
     assert lib.rt_edt(None, bogus, 8, bogus, 8, 4, 4, None, None) == _native.RT_EINVAL
-    assert lib.rt_create(None, 0) == _native.RT_EINVAL
+    assert lib.rt_create(None, 0, 0) == _native.RT_EINVAL
+    assert lib.rt_set_limits(None, 1, 1) == _native.RT_EINVAL
+    assert lib.rt_feature_norm(None, bogus, 4, bogus, None) == _native.RT_EINVAL
+
+
+def _tiles(shapes):
+    from paper_1405_7958_gb300 import _native
+    tiles = (_native.RtTile * len(shapes))()
+    for t, (H, W) in zip(tiles, shapes):
+        t.H, t.W = H, W
+        t.img = t.labels = t.d2 = 1
+        t.ld_img = t.ld_labels = t.ld_d2 = W
+    return tiles
+
+
+def test_segment_workspace_query_without_gpu(built):
+    """The batch workspace figure is computed on the host: positive, at
+    least the compulsory per-tile buffers, the largest chunk of 32 tiles, and
+    0 for invalid arguments."""
+    from paper_1405_7958_gb300 import _native
+    lib = _native.load(built)
+    p = _native.RtSegParams()
+    lib.rt_seg_params_default(ctypes.byref(p))
+    one = lib.rt_segment_workspace_bytes(_tiles([(4096, 4096)]), 1, ctypes.byref(p))
+    # padded R and mask copies (2 B/px), the binary image (1), union-find arrays (>= 10)
+    assert one >= 13 * 4096 * 4096
+    two = lib.rt_segment_workspace_bytes(_tiles([(4096, 4096)] * 2), 2, ctypes.byref(p))
+    assert two >= 2 * one - 4096
+    # 33 tiles run as a chunk of 32 and a chunk of 1: the figure is the larger chunk
+    small = [(512, 600)] * 33
+    w33 = lib.rt_segment_workspace_bytes(_tiles(small), 33, ctypes.byref(p))
+    w32 = lib.rt_segment_workspace_bytes(_tiles(small), 32, ctypes.byref(p))
+    assert w33 == w32
+    bad = _tiles([(0, 5)])
+    assert lib.rt_segment_workspace_bytes(bad, 1, ctypes.byref(p)) == 0
+    p.conn_recon = 5
+    assert lib.rt_segment_workspace_bytes(_tiles([(64, 64)]), 1, ctypes.byref(p)) == 0

@@ -1,0 +1,152 @@
+"""GPU tests of the boundary's bounds and sizing: an iteration bound or a
+time bound that runs out stops the propagation with RT_ETIMEOUT and leaves
+the context usable (the next call gives the oracle's bytes); a batch of more
+than 32 uneven tiles (two chunks) eager and replayed from a CUDA graph,
+every tile against the oracle; a context reserved with the library's
+workspace figure never grows; the feature normalisation against numpy."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import paper_1405_7958_gb300 as rt
+    return rt
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("variant", ["RT_RASTER", "RT_QUEUE", "RT_HYBRID"])
+def test_visit_bound_runs_out_and_context_recovers(rt, variant):
+    """A spiral corridor needs many visits of each of its 15 tiles; with one
+    visit per tile allowed the propagation stops with RT_ETIMEOUT, below the
+    reconstruction (it only ever raises pixels towards it)."""
+    I = synth.spiral(129, low=0)
+    J = np.zeros_like(I)
+    J[0, 0] = I[0, 0]
+    want = oracle.recon(J, I, 8)
+    ctx = rt.Context()
+    v = getattr(rt, variant)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.set_limits(max_iters=1)
+    got = host(rt.reconstruct(dev(I), dev(J), conn=8, variant=v, status=st, ctx=ctx))
+    assert int(st.item()) == rt.RT_ETIMEOUT
+    assert (got <= want).all() and not np.array_equal(got, want)
+    ctx.set_limits(0, 0)
+    got = host(rt.reconstruct(dev(I), dev(J), conn=8, variant=v, status=st, ctx=ctx))
+    assert int(st.item()) == rt.RT_OK
+    assert np.array_equal(got, want)
+    ctx.close()
+
+
+def test_time_bound_runs_out_and_context_recovers(rt):
+    """A 768 x 768 spiral's front crosses thousands of tile edges one after
+    another (each ring of the corridor crosses every tile on its way); 2 ms
+    of device time is not enough."""
+    I = synth.spiral(768, low=0)
+    J = np.zeros_like(I)
+    J[0, 0] = I[0, 0]
+    ctx = rt.Context()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.set_limits(timeout_ms=2)
+    rt.reconstruct(dev(I), dev(J), conn=8, status=st, ctx=ctx)
+    assert int(host(st)[0]) == rt.RT_ETIMEOUT
+    ctx.set_limits(0, 0)
+    got = host(rt.reconstruct(dev(I), dev(J), conn=8, status=st, ctx=ctx))
+    assert int(st.item()) == rt.RT_OK
+    assert np.array_equal(got, oracle.recon(J, I, 8))
+    ctx.close()
+
+
+def test_chain_visit_bound_in_params(rt):
+    """rt_seg_params.max_iters bounds the chain's propagation the same way:
+    the tile's status says RT_ETIMEOUT; the same call without the bound on
+    the same context gives the oracle's outputs."""
+    I = synth.spiral(300, low=0, high=60)      # dark corridor: R < 80 along it
+    ctx = rt.Context()
+    out = rt.segment_batch([dev(I)], rt.SegParams(max_iters=1), ctx=ctx)[0]
+    assert int(host(out["status"])[0]) == rt.RT_ETIMEOUT
+    out = rt.segment_batch([dev(I)], rt.SegParams(), outputs=[out], ctx=ctx)[0]
+    assert int(host(out["status"])[0]) == rt.RT_OK
+    want = oracle.chain(I)
+    for k in ("R", "F", "L", "D"):
+        assert np.array_equal(host(out[k]), want[k])
+    ctx.close()
+
+
+def test_batch_of_40_uneven_tiles_eager_and_graph(rt):
+    """40 tiles of ragged uneven sizes run as a chunk of 32 and a chunk of 8
+    in one call, eager and replayed from a CUDA graph: every output of every
+    tile equals the oracle's."""
+    specs = synth.batch_sizes(40, 77, lo=33, hi=33 + 29 * 14, step=29)
+    imgs = [synth.tile(H, W, s, ns) for H, W, ns, s in specs]
+    want = [oracle.chain(x) for x in imgs]
+    d = [dev(x) for x in imgs]
+    ctx = rt.Context()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        outs = rt.segment_batch(d, ctx=ctx, stream=s)
+    s.synchronize()
+    for o, w in zip(outs, want):
+        assert int(host(o["status"])[0]) == 0
+        assert int(host(o["n_kept"])[0]) == w["n_kept"]
+        for k in ("R", "F", "L", "D"):
+            assert np.array_equal(host(o[k]), w[k])
+    for o in outs:
+        for k in ("R", "F", "L", "D", "n_kept"):
+            o[k].fill_(-7 if o[k].dtype == torch.int32 else 7)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rt.segment_batch(d, outputs=outs, ctx=ctx, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for o, w in zip(outs, want):
+        assert int(host(o["n_kept"])[0]) == w["n_kept"]
+        for k in ("R", "F", "L", "D"):
+            assert np.array_equal(host(o[k]), w[k])
+    ctx.close()
+
+
+def test_reserved_workspace_is_enough(rt):
+    shapes = [(700, 1031), (64, 4000), (1024, 1024)]
+    imgs = [synth.config2_tile(40 + i, H=H, W=W) for i, (H, W) in enumerate(shapes)]
+    need = rt.segment_workspace_bytes(shapes)
+    assert need > 0
+    ctx = rt.Context(workspace_bytes=need)
+    have = ctx.workspace_bytes()
+    assert have >= need
+    outs = rt.segment_batch([dev(x) for x in imgs], ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.workspace_bytes() == have
+    for o, x in zip(outs, imgs):
+        w = oracle.chain(x)
+        assert np.array_equal(host(o["L"]), w["L"]) and np.array_equal(host(o["D"]), w["D"])
+    ctx.close()
+
+
+def test_feature_norm_matches_numpy(rt):
+    rng = np.random.default_rng(5)
+    x = (rng.normal(size=(1000, 24)) * rng.uniform(0.1, 50, size=24) + rng.normal(size=24) * 100).astype(np.float32)
+    x[:, 7] = 3.0                                           # a constant column: sd clamped to 1e-6
+    pk = rt.Picker(seed=0)
+    pk.set_norm(dev(x))
+    norm = host(pk.norm)
+    xd = x.astype(np.float64)
+    assert np.allclose(norm[:24], xd.mean(axis=0), rtol=1e-6, atol=1e-6)
+    sd = np.maximum(xd.std(axis=0, ddof=1), 1e-6)
+    assert np.allclose(norm[24:], sd, rtol=1e-6)
+    assert norm[24 + 7] == np.float32(1e-6)
