@@ -225,8 +225,11 @@ RT_API rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iteration
  * library (about 2.5 MiB, held on every GPU that loads the library until
  * the process exits), so images are limited to H * W <= 1,048,576 pixels
  * (and W <= 32768); larger ones return RT_ESIZE. It runs on the current
- * device; the first call on a device looks the array's address up once, so
- * make that first call before any stream capture. All calls share the one
+ * device. The first call on a device looks the array's address up once;
+ * that first call may also load the library's module onto the device,
+ * which places the array there and may synchronise the device. So make
+ * one warm-up call at start-up, before reserving a memory budget and
+ * before any stream capture. All calls share the one
  * array: calls whose work overlaps on the GPU (other streams, other host
  * threads) race on it and must be serialised by the caller. Arguments,
  * output and status are as for rt_edt.

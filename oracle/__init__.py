@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_OBJ = os.path.join(_HERE, "objects.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -32,9 +33,10 @@ _i64p = ctypes.POINTER(ctypes.c_long)
 
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so (plain C, -O2, no vector intrinsics)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in (_SRC, _SRC_OBJ))
+    if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_OBJ, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -58,6 +60,10 @@ def _load():
             lib.orc_edt_meijster.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, _i32p]
             lib.orc_edt_at.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.orc_edt_at.restype = ctypes.c_int64
+            lib.orc_object_features.argtypes = [_i32p, _u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p,
+                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+            lib.orc_watershed.argtypes = [_i32p, _i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p,
+                                          ctypes.POINTER(ctypes.c_int)]
             lib.orc_chain.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       _u8p, _u8p, _i32p, _i32p, _i32p]
@@ -177,3 +183,48 @@ def chain(I: np.ndarray, h: int = 30, conn_recon: int = 8, t: int = 80, conn_fil
                              int(min_area), int(max_area), _p(R, _u8p), _p(F, _u8p), _p(L, _i32p),
                              _p(D, _i32p), ctypes.byref(n)), "chain")
     return {"R": R, "F": F, "L": L, "D": D, "n_kept": n.value}
+
+
+NFEAT = 20
+FEATURE_NAMES = ("area", "perimeter", "bbox_h", "bbox_w", "centroid_r", "centroid_c", "major_axis", "minor_axis",
+                 "eccentricity", "compactness", "mean", "std", "min", "max", "median", "entropy", "glcm_pairs",
+                 "glcm_contrast", "glcm_energy", "glcm_homogeneity")
+# features whose values are integers (compared exactly)
+INTEGER_FEATURES = (0, 1, 2, 3, 12, 13, 14, 16)
+
+
+def _i32(a: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a)
+    if a.dtype != np.int32 or a.ndim != 2:
+        raise TypeError("expected a 2-D int32 array")
+    return a
+
+
+def object_features(L: np.ndarray, I: np.ndarray):
+    """Per-object features of the label image L (>= 0: object label) over the
+    intensities I: (labels ascending, float64 n x 20). See objects.c."""
+    L, I = _i32(L), _u8(I)
+    if L.shape != I.shape:
+        raise ValueError("shape mismatch")
+    n = ctypes.c_int(0)
+    _check(_load().orc_object_features(_p(L, _i32p), _p(I, _u8p), L.shape[0], L.shape[1], 0, None, None,
+                                       ctypes.byref(n)), "object_features")
+    labels = np.empty(max(n.value, 1), dtype=np.int32)
+    feat = np.empty((max(n.value, 1), NFEAT), dtype=np.float64)
+    _check(_load().orc_object_features(_p(L, _i32p), _p(I, _u8p), L.shape[0], L.shape[1], n.value,
+                                       _p(labels, _i32p), feat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       ctypes.byref(n)), "object_features")
+    return labels[:n.value], feat[:n.value]
+
+
+def watershed(L: np.ndarray, D: np.ndarray, h: int = 2, return_count: bool = False):
+    """Marker-controlled watershed of the distance map D inside every object
+    of L (basin label per object pixel, -1 elsewhere). See objects.c."""
+    L, D = _i32(L), _i32(D)
+    if L.shape != D.shape:
+        raise ValueError("shape mismatch")
+    B = np.empty_like(L)
+    n = ctypes.c_int(0)
+    _check(_load().orc_watershed(_p(L, _i32p), _p(D, _i32p), L.shape[0], L.shape[1], int(h), _p(B, _i32p),
+                                 ctypes.byref(n)), "watershed")
+    return (B, n.value) if return_count else B
