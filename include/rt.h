@@ -194,7 +194,9 @@ enum {
     RT_PHASE_LABEL = 4,        /* labeling and area filter */
     RT_PHASE_EDT = 5,          /* distance transform */
     RT_PHASE_PICK = 6,         /* features and picker network */
-    RT_NPHASES = 7
+    RT_PHASE_OBJECTS = 7,      /* per-object features */
+    RT_PHASE_WATERSHED = 8,    /* watershed */
+    RT_NPHASES = 9
 };
 
 /*
@@ -212,6 +214,61 @@ RT_API rt_status rt_timing_enable(rt_ctx *ctx, int enable);
 RT_API rt_status rt_timing_read(rt_ctx *ctx, double *ms, int64_t *count, int reset);
 RT_API int64_t rt_kernel_launches(const rt_ctx *ctx);
 RT_API rt_status rt_recon_stats(rt_ctx *ctx, int64_t *visits, int64_t *iterations, int64_t *pops);
+
+/*
+ * Watershed (Section 5.1: the step after Pre-Watershed that splits touching
+ * nuclei), marker-controlled flooding of the squared distance map `d2`
+ * inside every object of `labels`; objects never exchange pixels, and
+ * pixels are 8-connected within their object. Per object:
+ *   1. markers: the regional maxima of the h-maxima transform of d2 (the
+ *      reconstruction by dilation of max(d2 - h, 0) under d2, inside the
+ *      object): 8-connected plateaus of equal value without a higher
+ *      neighbour, each labelled by its smallest linear index r * W + c;
+ *   2. flooding by levels (Vincent-Soille geodesic influence zones): for
+ *      every distinct d2 value t of the object, highest first, the basins
+ *      grow in synchronous breadth-first layers into the pixels with
+ *      d2 >= t that have no basin yet; a pixel takes the smallest basin
+ *      label among its neighbours labelled in earlier layers.
+ * labels: int32 H x W (ld_lab) as rt_label_area writes them (-1 outside
+ * objects; an object's label is the linear index of its first pixel in
+ * raster order; other label images report RT_EINVAL in dev_status).
+ * d2: int32 H x W (ld_d2). h >= 0. basins: int32 H x W (ld_b), the basin
+ * label of every object pixel, -1 elsewhere; must not overlap the inputs.
+ * dev_n_basins (device int32, nullable) receives the number of markers.
+ * The workspace holds about 37 bytes per pixel.
+ */
+RT_API rt_status rt_watershed(rt_ctx *ctx, const int32_t *labels, int64_t ld_lab, const int32_t *d2,
+                              int64_t ld_d2, int H, int W, int h, int32_t *basins, int64_t ld_b,
+                              int32_t *dev_n_basins, int32_t *dev_status, void *stream);
+
+/*
+ * Feature computation stage (Section 5.1): per object of `labels` (as for
+ * rt_watershed), over the intensities `img`, RT_NOBJFEAT features, computed
+ * as the paper organises it: one thread block per object's minimum bounding
+ * box accumulates the intermediate results (pixel count, perimeter,
+ * coordinate and intensity moments, the 256-bin histogram, the 8-level
+ * co-occurrence matrix of horizontally adjacent pixels), then one thread
+ * per object computes the features. In order: area; perimeter (pixel edges
+ * between the object and a 4-neighbour outside it, the image border
+ * included); bounding box height, width; centroid row, column; major and
+ * minor axis 4 sqrt(l1), 4 sqrt(l2) (l1 >= l2 >= 0 the eigenvalues of the
+ * coordinates' population covariance); eccentricity sqrt(1 - l2 / l1) (0
+ * when l1 = 0); compactness 4 pi area / perimeter^2; intensity mean,
+ * population standard deviation, minimum, maximum, median (the smallest v
+ * with 2 #{I <= v} >= area), entropy of the histogram in bits;
+ * co-occurrence pairs n2 ((r, c), (r, c + 1) both in the object, levels
+ * I >> 5), contrast sum (a - b)^2 g / n2, energy sum g^2 / n2^2,
+ * homogeneity sum g / (1 + |a - b|) / n2 (0 for the last three if n2 = 0).
+ * obj_labels: int32[cap], feat: double[cap][RT_NOBJFEAT], both device,
+ * written for the first min(cap, number of objects) objects in increasing
+ * label order; dev_n_obj (device int32, nullable) receives the number of
+ * objects. The workspace holds about 28 bytes per pixel plus 1.4 KB per
+ * output slot.
+ */
+#define RT_NOBJFEAT 20
+RT_API rt_status rt_object_features(rt_ctx *ctx, const int32_t *labels, int64_t ld_lab, const uint8_t *img,
+                                    int64_t ld_img, int H, int W, int32_t *obj_labels, double *feat, int cap,
+                                    int32_t *dev_n_obj, int32_t *dev_status, void *stream);
 
 /*
  * The same squared EDT as rt_edt, for callers that must not allocate device

@@ -193,6 +193,43 @@ def edt(fg: torch.Tensor, *, out=None, status=None, ctx=None, stream=None):
     return out
 
 
+def watershed(labels: torch.Tensor, d2: torch.Tensor, h: int = 2, *, out=None, n_basins=None, status=None, ctx=None,
+              stream=None) -> torch.Tensor:
+    """Marker-controlled watershed of the squared distance map inside every
+    labelled object (int32 CUDA tensors); basin label per object pixel, -1
+    elsewhere."""
+    ctx = ctx or default_context(labels.device.index)
+    lp, lld = _dev_ptr(labels, torch.int32, "labels")
+    dp, dld = _dev_ptr(d2, torch.int32, "d2")
+    H, W = labels.shape
+    out = torch.empty((H, W), dtype=torch.int32, device=labels.device) if out is None else out
+    op, old = _dev_ptr(out, torch.int32, "out")
+    np_ = None if n_basins is None else n_basins.data_ptr()
+    sp = None if status is None else status.data_ptr()
+    _check(lib().rt_watershed(ctx.handle, lp, lld, dp, dld, H, W, int(h), op, old, np_, sp, _stream(stream)),
+           "rt_watershed")
+    return out
+
+
+def object_features(labels: torch.Tensor, image: torch.Tensor, cap: int, *, n_obj=None, status=None, ctx=None,
+                    stream=None):
+    """Per-object features of the labelled objects over the uint8 image:
+    (labels int32[cap], features float64[cap, 20]) for the first min(cap, n)
+    objects in label order; n_obj (device int32[1]) receives n."""
+    ctx = ctx or default_context(labels.device.index)
+    lp, lld = _dev_ptr(labels, torch.int32, "labels")
+    ip, ild = _dev_ptr(image, torch.uint8, "image")
+    H, W = labels.shape
+    dev = labels.device
+    olab = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    feat = torch.empty((max(cap, 1), _native.RT_NOBJFEAT), dtype=torch.float64, device=dev)
+    np_ = None if n_obj is None else n_obj.data_ptr()
+    sp = None if status is None else status.data_ptr()
+    _check(lib().rt_object_features(ctx.handle, lp, lld, ip, ild, H, W, olab.data_ptr(), feat.data_ptr(), int(cap),
+                                    np_, sp, _stream(stream)), "rt_object_features")
+    return olab[:cap], feat[:cap]
+
+
 def synth_tile(H: int, W: int, seed: int, n_shapes: int, *, kind: str = "ellipse", vlo: int = 30, vhi: int = 100,
                rmin: int = 4, rmax: int = 12, amin: int = 4, amax: int = 14, background: str = "perlin",
                noise: bool = True, out=None, device=None, ctx=None, stream=None) -> torch.Tensor:

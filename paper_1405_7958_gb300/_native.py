@@ -20,10 +20,11 @@ EXPORTS = (
     "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_recon_stats",
     "rt_edt_noalloc", "rt_synth_tile", "rt_tile_features", "rt_mlp_forward", "rt_mlp_backward",
     "rt_mlp_adamw", "rt_set_picker", "rt_last_picks", "rt_set_limits", "rt_segment_workspace_bytes",
-    "rt_feature_norm",
+    "rt_feature_norm", "rt_watershed", "rt_object_features",
 )
-RT_NPHASES = 7
-PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt", "pick")
+RT_NPHASES = 9
+PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt", "pick", "objects", "watershed")
+RT_NOBJFEAT = 20
 RT_NFEATURES = 24
 RT_MLP_NPARAM = 5955
 RT_POLICY_PLAIN, RT_POLICY_LEARNED = 0, 1
@@ -76,6 +77,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_label_area.restype = _int
     lib.rt_edt.argtypes = [_vp, _vp, _i64, _vp, _i64, _int, _int, _vp, _vp]
     lib.rt_edt.restype = _int
+    lib.rt_watershed.argtypes = [_vp, _vp, _i64, _vp, _i64, _int, _int, _int, _vp, _i64, _vp, _vp, _vp]
+    lib.rt_watershed.restype = _int
+    lib.rt_object_features.argtypes = [_vp, _vp, _i64, _vp, _i64, _int, _int, _vp, _vp, _int, _vp, _vp, _vp]
+    lib.rt_object_features.restype = _int
     lib.rt_edt_noalloc.argtypes = [_vp, _i64, _vp, _i64, _int, _int, _vp, _vp]
     lib.rt_edt_noalloc.restype = _int
     lib.rt_synth_tile.argtypes = [_vp, _vp, _i64, _int, _int, ctypes.c_uint64] + [_int] * 10 + [_vp]

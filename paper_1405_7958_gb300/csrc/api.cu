@@ -12,6 +12,7 @@
 #include "features.cuh"
 #include "fill.cuh"
 #include "mlp.cuh"
+#include "objects.cuh"
 #include "recon.cuh"
 #include "synth.cuh"
 
@@ -678,6 +679,73 @@ rt_status rt_edt(rt_ctx *ctx, const uint8_t *fg, int64_t ld_fg, int32_t *d2, int
     Phase ph(ctx, RT_PHASE_EDT, s);
     ctx->launches += 3;
     return cuda_status(launch_edt(a, s));
+}
+
+rt_status rt_watershed(rt_ctx *ctx, const int32_t *labels, int64_t ld_lab, const int32_t *d2, int64_t ld_d2, int H,
+                       int W, int h, int32_t *basins, int64_t ld_b, int32_t *dev_n_basins, int32_t *dev_status,
+                       void *stream)
+{
+    if (!ctx || !labels || !d2 || !basins || bad_dims(H, W) || ld_lab < W || ld_d2 < W || ld_b < W || h < 0)
+        return RT_EINVAL;
+    const size_t nb = span(H, ld_b, 4, W);
+    if (overlaps(basins, nb, labels, span(H, ld_lab, 4, W)) || overlaps(basins, nb, d2, span(H, ld_d2, 4, W)))
+        return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    rt_status st = ensure_ws(ctx, obj_workspace_bytes(H, W, false, true, 0));
+    if (st != RT_OK) return st;
+    ObjArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.L = labels;
+    a.ld_L = ld_lab;
+    a.D = d2;
+    a.ld_D = ld_d2;
+    a.H = H;
+    a.W = W;
+    a.h = h;
+    a.basins = basins;
+    a.ld_B = ld_b;
+    a.n_basins = dev_n_basins;
+    obj_carve(a, (char *)ctx->ws, false, true);
+    a.err = dev_status;
+    if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
+    Phase ph(ctx, RT_PHASE_WATERSHED, s);
+    int n = 0;
+    const cudaError_t e = launch_watershed(a, ctx->num_sms, s, &n);
+    ctx->launches += n;
+    return cuda_status(e);
+}
+
+rt_status rt_object_features(rt_ctx *ctx, const int32_t *labels, int64_t ld_lab, const uint8_t *img, int64_t ld_img,
+                             int H, int W, int32_t *obj_labels, double *feat, int cap, int32_t *dev_n_obj,
+                             int32_t *dev_status, void *stream)
+{
+    if (!ctx || !labels || !img || bad_dims(H, W) || ld_lab < W || ld_img < W || cap < 0) return RT_EINVAL;
+    if (cap > 0 && (!obj_labels || !feat)) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    rt_status st = ensure_ws(ctx, obj_workspace_bytes(H, W, true, false, cap));
+    if (st != RT_OK) return st;
+    ObjArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.L = labels;
+    a.ld_L = ld_lab;
+    a.I = img;
+    a.ld_I = ld_img;
+    a.H = H;
+    a.W = W;
+    a.cap = cap;
+    a.out_labels = obj_labels;
+    a.feat = feat;
+    a.n_obj = dev_n_obj;
+    obj_carve(a, (char *)ctx->ws, true, false);
+    a.err = dev_status;
+    if (dev_status) RT_CUDA_TRY(cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s));
+    Phase ph(ctx, RT_PHASE_OBJECTS, s);
+    int n = 0;
+    const cudaError_t e = launch_object_features(a, ctx->num_sms, s, &n);
+    ctx->launches += n;
+    return cuda_status(e);
 }
 
 rt_status rt_synth_tile(rt_ctx *ctx, uint8_t *out, int64_t ld, int H, int W, uint64_t seed, int n_shapes, int kind,
