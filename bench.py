@@ -439,6 +439,64 @@ def config3_leg(rt, ctx, dev, stream_ctor):
 
 
 
+def timed_ms(fn, reps):
+    """Median milliseconds of fn() on the current stream (CUDA events)."""
+    import torch
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def objects_leg(rt, ctx, outs, imgs):
+    """The steps after the chain on the bench's tiles: per-nucleus features
+    (rt_object_features) and the watershed of the distance map (rt_watershed,
+    h = 2), one tile per call; median of 5 after a warm-up call."""
+    import torch
+    cap = 20000
+    n_obj = torch.zeros(1, dtype=torch.int32, device=imgs[0].device)
+    n_bas = torch.zeros(1, dtype=torch.int32, device=imgs[0].device)
+    basins = [torch.empty_like(o["L"]) for o in outs]
+
+    def feats():
+        for o, im in zip(outs, imgs):
+            rt.object_features(o["L"], im, cap, n_obj=n_obj, ctx=ctx)
+
+    def sheds():
+        for o, b in zip(outs, basins):
+            rt.watershed(o["L"], o["D"], 2, out=b, n_basins=n_bas, ctx=ctx)
+
+    feats()
+    sheds()
+    f_ms, w_ms = timed_ms(feats, 5), timed_ms(sheds, 5)
+    nobj, nbas = int(n_obj.item()), int(n_bas.item())
+    n = len(imgs)
+    return {"tiles": n, "features_ms_per_tile": f_ms / n, "watershed_ms_per_tile": w_ms / n,
+            "nuclei_last_tile": nobj, "basins_last_tile": nbas,
+            "nuclei_features_per_s": nobj * n / (f_ms / 1000.0) if nobj else None,
+            "features_per_nucleus": 20, "watershed_h": 2}
+
+
+def slide_leg(rt, ctx, side=16384):
+    """Whole-slide segmentation: one side x side slide (16 tiles of 4096^2,
+    nuclei across every seam) as one image; median of 3 after a warm-up."""
+    import torch
+    slide = rt.config2_tile(515151, H=side, W=side, ctx=ctx)
+    out = rt.segment_batch([slide], ctx=ctx, want_recon=False, want_filled=False)
+    ms = timed_ms(lambda: rt.segment_batch([slide], outputs=out, ctx=ctx, want_recon=False, want_filled=False), 3)
+    ok = int(out[0]["status"].item()) == 0
+    res = {"side": side, "ms": ms, "status_ok": ok, "megapixels_s": side * side / 1e6 / (ms / 1000.0),
+           "tile4k_equiv_s": side * side / 2 ** 24 / (ms / 1000.0), "nuclei_kept": int(out[0]["n_kept"].item())}
+    del out, slide
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_native(a, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -500,6 +558,17 @@ def run_native(a, rank, world, local_rank):
     px = a.size * a.size
     value = world * a.batch * a.steps / (total_ms / 1000.0)
 
+    # the propagation launch alone: the same steps on one stream (no other
+    # step's kernels beside it), for the kernel's own duration
+    pipe1 = Pipeline(rt, dev, 1, picker)
+    outs_a = [None]
+
+    def step_alone(k, c, s):
+        outs_a[0] = rt.segment_batch(imgs, learned, outputs=outs_a[0], ctx=c, stream=s)
+
+    _, _, _, phases_alone = pipe1.run(step_alone, max(5, a.steps // 4), a.warmup, barrier, timing=True)
+    pipe1.close()
+
     # the plain legs on the same harness (same streams, contexts, flushes)
     k2 = max(5, a.steps // 4)
     plain_ms, _, plain_launches, _ = pipe.run(step_plain, k2, a.warmup, barrier)
@@ -515,6 +584,8 @@ def run_native(a, rank, world, local_rank):
     # timed runs after 20 warm-up runs, with the bytes the passes moved
     config1 = None
     config3 = None
+    objects = None
+    slide = None
     stream = torch.cuda.current_stream()
     if not a.no_configs and world == 1:
         import synth
@@ -536,14 +607,17 @@ def run_native(a, rank, world, local_rank):
                    "pass_bytes": it1 * PASSES_PER_ITERATION * TILE_PX * BYTES_PASS,
                    "compulsory_bytes": BYTES_RECON * 512 * 512}
         config3 = config3_leg(rt, ctx, dev, lambda: torch.cuda.Stream(device=dev))
+        objects = objects_leg(rt, ctx, outs_l[0], imgs)
+        slide = slide_leg(rt, ctx)
 
     serving = None
     if a.serve_seconds > 0 and world == 1:
         from paper_1405_7958_gb300 import serve
         spool = serve.make_pool(32, 5000, ctx=ctx)
-        serve.run_batched(serve.arrivals(50.0, 0.3, len(spool), 9, spool), spool, policy=1, picker=picker)
+        hp = serve.host_pool(spool)
+        serve.run_batched(serve.arrivals(800.0, 1.0, len(spool), 9, spool), spool, policy=1, picker=picker, hp=hp)
         reqs = serve.arrivals(800.0, a.serve_seconds, len(spool), 801, spool)
-        serve.run_batched(reqs, spool, policy=1, picker=picker)
+        serve.run_batched(reqs, spool, policy=1, picker=picker, hp=hp)
         serving = {"rate_tiles_s": 800, "seconds": a.serve_seconds, "tiles": "512..4096 px sides",
                    **serve.summarize(reqs, a.serve_seconds)}
 
@@ -557,7 +631,11 @@ def run_native(a, rank, world, local_rank):
         ach = algo_bytes / per_launch_s / 1e9
         its = visits[1]       # dense tile iterations of one step (the last one)
         pass_bytes = its * PASSES_PER_ITERATION * TILE_PX * BYTES_PASS
+        ms_alone, n_alone = phases_alone["recon_sweep"]
+        alone_s = ms_alone / max(n_alone, 1) / 1000.0
         roof = {"kernel": "recon_persistent_kernel<8,0>", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "launch_ms_alone": alone_s * 1000, "achieved_alone": algo_bytes / alone_s / 1e9,
+                "frac_alone": algo_bytes / alone_s / 1e9 / peak,
                 "frac": ach / peak, "peak_source": peak_kind, "traffic": profiled_traffic(),
                 "algorithmic_bytes_per_launch": algo_bytes, "launch_ms": per_launch_s * 1000,
                 "pass_bytes_per_launch": pass_bytes, "pass_equivalent_gbs": pass_bytes / per_launch_s / 1e9,
@@ -667,6 +745,8 @@ def run_native(a, rank, world, local_rank):
             "serving_batched_learned": serving,
             "config1_recon_512": config1,
             "config3_uneven_64_graph": config3,
+            "objects_per_tile": objects,
+            "slide": slide,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -1,14 +1,19 @@
 """Serving loop with continuous batching for the segmentation chain.
 
 Requests (single tiles, sides 512..4096) arrive as a Poisson process. The
-batched server admits arrived requests while their device memory fits the
-budget, launches every admitted group as one batch on a free stream (one
-library context per stream), and keeps admitting and launching while
-earlier batches are still on the GPU, so host-to-device copies, compute and
-device-to-host copies of different batches overlap. The plain server runs
-one tile at a time on one stream with the fixed variant. Latency is the
-time from a request's arrival to its labels and distance map being in host
-memory.
+batched server reserves, at start-up, one library context per stream with
+the workspace of the largest batch it will launch (the library's exact
+figure, rt_segment_workspace_bytes), so nothing is allocated inside the
+loop; the rest of the device-memory budget holds the requests' own buffers
+(input, labels, distances: 9 bytes per pixel). It admits arrived requests,
+in arrival order, while their buffers fit the budget beside those in use
+and the batch's workspace fits the context's reservation, launches every
+admitted group as one batch on a free stream, and keeps admitting and
+launching while earlier batches are still on the GPU, so host-to-device
+copies, compute and device-to-host copies of different batches overlap.
+The plain server runs one tile at a time on one stream with the fixed
+variant. Latency is the time from a request's arrival to its labels and
+distance map being in host memory.
 
     python -m paper_1405_7958_gb300.serve --rates 50 200 800 --duration 10
 """
@@ -24,7 +29,8 @@ import torch
 
 import paper_1405_7958_gb300 as rt
 
-BYTES_PER_PX = 30   # input 1 + labels 4 + EDT 4 + R 1 + F 1 + workspace ~19 (padded copies, union-find, EDT)
+BYTES_PER_PX = 9            # a request's device buffers: input 1 + labels 4 + distances 4
+BATCH_TILES_4K = 8          # the largest batch a context reserves workspace for, in 4096^2 tiles
 
 
 @dataclass
@@ -50,10 +56,17 @@ class Batch:
 
 class PinnedPool:
     """Reusable pinned host buffers by shape (allocating pinned memory per
-    request would stall the loop)."""
+    request would stall the loop); reserve() allocates them before the
+    timed run."""
 
     def __init__(self):
         self.free = {}
+
+    def reserve(self, shapes, per_shape: int, dtype=torch.int32):
+        for shape in set(tuple(x) for x in shapes):
+            lst = self.free.setdefault((shape, dtype), [])
+            while len(lst) < per_shape:
+                lst.append(torch.empty(shape, dtype=dtype).pin_memory())
 
     def get(self, shape, dtype=torch.int32):
         lst = self.free.get((shape, dtype))
@@ -111,26 +124,41 @@ def _release(r, hp: PinnedPool, keep: bool):
         r.out_L = r.out_D = None
 
 
-def admit(pending: list, in_use: int, budget_bytes: int, max_batch: int):
+def request_bytes(r) -> int:
+    return r.H * r.W * BYTES_PER_PX
+
+
+def admit(pending: list, in_use: int, budget_bytes: int, max_batch: int, ws_fits=None):
     """Takes requests from the front of `pending` (arrival order) while their
-    device bytes fit the budget beside the bytes in use, at most max_batch; a
-    request larger than the whole budget is taken alone once nothing else is
-    in use. Returns (taken requests, bytes in use)."""
+    device bytes fit the budget beside the bytes in use, at most max_batch,
+    and (with ws_fits) while the batch's workspace fits the context's
+    reservation; a request larger than the whole budget is taken alone once
+    nothing else is in use. Returns (taken requests, bytes in use)."""
     take = []
     while pending and len(take) < max_batch:
-        need = pending[0].H * pending[0].W * BYTES_PER_PX
+        need = request_bytes(pending[0])
         if in_use + need > budget_bytes and (take or in_use > 0):
+            break
+        if take and ws_fits is not None and not ws_fits([(r.H, r.W) for r in take] + [(pending[0].H, pending[0].W)]):
             break
         in_use += need
         take.append(pending.pop(0))
     return take, in_use
 
 
-def run_plain(reqs, pool, variant=rt.RT_RASTER, ctx=None, keep: bool = False):
+def host_pool(pool, per_shape: int = 8) -> PinnedPool:
+    """Pinned read-back buffers for every tile shape of the pool (two per
+    request: labels and distances), allocated before the timed run."""
+    hp = PinnedPool()
+    hp.reserve([t.shape for t in pool], 2 * per_shape)
+    return hp
+
+
+def run_plain(reqs, pool, variant=rt.RT_RASTER, ctx=None, keep: bool = False, hp: PinnedPool | None = None):
     """One tile at a time, fixed variant, one stream."""
     ctx = ctx or rt.Context()
     s = torch.cuda.Stream()
-    hp = PinnedPool()
+    hp = hp or PinnedPool()
     params = rt.SegParams(variant=variant)
     t0 = time.perf_counter()
     for r in reqs:
@@ -146,16 +174,23 @@ def run_plain(reqs, pool, variant=rt.RT_RASTER, ctx=None, keep: bool = False):
 
 
 def run_batched(reqs, pool, budget_bytes: int = 40 << 30, max_batch: int = 32, n_streams: int = 3,
-                policy: int = 0, picker=None, keep: bool = False):
+                policy: int = 0, picker=None, keep: bool = False, hp: PinnedPool | None = None):
     """Continuous batching under a device-memory budget (policy 1: the
     attached picker chooses each tile's variant)."""
-    hp = PinnedPool()
+    hp = hp or PinnedPool()
     streams = [torch.cuda.Stream() for _ in range(n_streams)]
-    ctxs = [rt.Context() for _ in range(n_streams)]
+    params = rt.SegParams(policy=policy)
+    reserve = rt.segment_workspace_bytes([(4096, 4096)] * BATCH_TILES_4K, params)
+    ctxs = [rt.Context(workspace_bytes=reserve) for _ in range(n_streams)]
+    held = [c.workspace_bytes() for c in ctxs]
+    budget_bytes -= sum(held)
     if picker is not None:
         for c in ctxs:
             picker.attach(c)
-    params = rt.SegParams(policy=policy)
+
+    def ws_fits(shapes):
+        return rt.segment_workspace_bytes(shapes, params) <= reserve
+
     busy = [None] * n_streams
     pending, nxt, done_n = [], 0, 0
     in_use = 0
@@ -171,14 +206,14 @@ def run_batched(reqs, pool, budget_bytes: int = 40 << 30, max_batch: int = 32, n
                 tnow = time.perf_counter() - t0
                 for r in b.reqs:
                     r.done = tnow
-                    in_use -= r.H * r.W * BYTES_PER_PX
+                    in_use -= request_bytes(r)
                     _release(r, hp, keep)
                 done_n += len(b.reqs)
                 busy[k] = None
         # admit and launch on a free stream
         free = [k for k, b in enumerate(busy) if b is None]
         if pending and free:
-            take, in_use = admit(pending, in_use, budget_bytes, max_batch)
+            take, in_use = admit(pending, in_use, budget_bytes, max_batch, ws_fits)
             if take:
                 k = free[0]
                 s = streams[k]
@@ -196,8 +231,11 @@ def run_batched(reqs, pool, budget_bytes: int = 40 << 30, max_batch: int = 32, n
             _wait_until(t0, min(reqs[nxt].arrival, (time.perf_counter() - t0) + 1e-4))
         else:
             time.sleep(2e-5)
+    grown = [c.workspace_bytes() != h for c, h in zip(ctxs, held)]
     for c in ctxs:
         c.close()
+    if any(grown):
+        raise RuntimeError("a serving context grew its workspace inside the loop")
     return reqs
 
 
@@ -215,13 +253,15 @@ def summarize(reqs, duration: float) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--rates", type=float, nargs="+", default=[50, 200, 800])
-    ap.add_argument("--duration", type=float, default=10.0)
+    ap.add_argument("--duration", type=float, default=30.0)
+    ap.add_argument("--warmup", type=float, default=2.0, help="seconds of arrivals at the same rate first")
     ap.add_argument("--pool", type=int, default=48)
     ap.add_argument("--picker", default=None, help="trained picker weights (.npz) for the batched server")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     ctx = rt.Context()
     pool = make_pool(a.pool, 5000, ctx=ctx)
+    hp = host_pool(pool)
     picker = None
     if a.picker:
         from paper_1405_7958_gb300 import picker as pk
@@ -231,17 +271,17 @@ def main():
         res[str(lam)] = {}
         for mode in ("plain", "batched"):
             reqs = arrivals(lam, a.duration, len(pool), int(lam) * 7 + 1, pool)
-            # warm-up on a few requests (allocations, first launches)
-            warm = arrivals(20.0, 0.3, len(pool), 99, pool)
+            # warm-up at the same rate (first launches, torch's caching allocator)
+            warm = arrivals(lam, a.warmup, len(pool), 99, pool)
             if mode == "plain":
-                run_plain(warm, pool, ctx=ctx)
+                run_plain(warm, pool, ctx=ctx, hp=hp)
                 torch.cuda.synchronize()
-                run_plain(reqs, pool, ctx=ctx)
+                run_plain(reqs, pool, ctx=ctx, hp=hp)
             else:
                 pol = 1 if picker is not None else 0
-                run_batched(warm, pool, policy=pol, picker=picker)
+                run_batched(warm, pool, policy=pol, picker=picker, hp=hp)
                 torch.cuda.synchronize()
-                run_batched(reqs, pool, policy=pol, picker=picker)
+                run_batched(reqs, pool, policy=pol, picker=picker, hp=hp)
             res[str(lam)][mode] = summarize(reqs, a.duration)
             print(json.dumps({"rate": lam, "mode": mode, **res[str(lam)][mode]}), flush=True)
     if a.out:

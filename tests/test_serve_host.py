@@ -65,3 +65,14 @@ def test_summary_percentiles():
     end = max(r.done for r in reqs)
     assert s["throughput_tiles_s"] == pytest.approx(100 / end)
     assert s["throughput_4k_equiv_s"] == pytest.approx(100 / end)
+
+
+def test_admission_keeps_the_batch_inside_the_reserved_workspace():
+    """With a workspace check, a batch stops growing at the first request
+    whose workspace would exceed the reservation (here: at most 3 tiles)."""
+    pend = [_req(k, 10, 10) for k in range(6)]
+    fits = lambda shapes: len(shapes) <= 3
+    take, used = serve.admit(pend, 0, 10 ** 9, 32, fits)
+    assert [r.rid for r in take] == [0, 1, 2] and used == 300 * serve.BYTES_PER_PX
+    take, _ = serve.admit(pend, 0, 10 ** 9, 32, lambda shapes: False)
+    assert [r.rid for r in take] == [3]              # a lone request is always taken
