@@ -521,7 +521,7 @@ def run_native(a, rank, world, local_rank):
     from paper_1405_7958_gb300 import picker as pkmod
     picker = pkmod.load(os.path.join(ROOT, "paper_1405_7958_gb300", "data", "picker_config4.npz"), device=dev)
     picker.attach(ctx)
-    learned = rt.SegParams(policy=1)
+    learned = rt.SegParams(policy=1, pick_min_prob=600)    # the trained picker with its confidence fall-back
     plain = rt.SegParams()
     nst = max(1, a.streams)
     pipe = Pipeline(rt, dev, nst, picker)

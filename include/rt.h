@@ -310,11 +310,13 @@ RT_API rt_status rt_synth_tile(rt_ctx *ctx, uint8_t *out, int64_t ld, int H, int
                                int amin, int amax, int flat, int noise, void *stream);
 
 /*
- * Learned variant picker. The paper's PATS scheduler (Section 3.2.1) orders
+ * Learned schedule picker. The paper's PATS scheduler (Section 3.2.1) orders
  * tasks by estimated speedup because the run time of its irregular
  * operations cannot be estimated in advance; here a small network reads 24
- * cheap statistics of a tile and picks the propagation variant of its
- * reconstruction (RT_RASTER, RT_QUEUE or RT_HYBRID, class index = variant - 1).
+ * cheap statistics of a tile and picks one of three schedules for its
+ * reconstruction: a propagation variant and its sweep iterations per dense
+ * tile visit (rt_set_picker_classes; by default RT_RASTER with 4, 12 and 24
+ * iterations: short visits win on small tiles, longer ones on large tiles).
  *
  * rt_tile_features: features of n tiles (host arrays of device pointers,
  * strides and sizes; n <= 32) into out, a device float array n x
@@ -342,7 +344,9 @@ RT_API rt_status rt_tile_features(rt_ctx *ctx, const uint8_t *const *imgs, const
  *
  * rt_mlp_forward: logits (B x 3, nullable), saved activations act (B x 128:
  * h1 then h2 after ReLU, nullable, needed by the backward pass) and the
- * argmax pick (B int32, nullable).
+ * argmax pick (B int32, nullable). Confidence fall-back: where the argmax's
+ * softmax probability 1 / sum_k exp(z_k - z_max) (fp32) is below min_prob,
+ * pick is `fallback` instead (min_prob <= 0: never).
  * rt_mlp_backward: gradient of the mean cross-entropy loss with respect to
  * every parameter into grad (RT_MLP_NPARAM fp32, overwritten), and the loss
  * into *loss (device float, nullable); label holds class indices 0..2. The
@@ -351,7 +355,8 @@ RT_API rt_status rt_tile_features(rt_ctx *ctx, const uint8_t *const *imgs, const
  * bf16(master) with round-to-nearest-even; m and v are the moment buffers.
  */
 RT_API rt_status rt_mlp_forward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, int B,
-                                float *logits, float *act, int32_t *pick, void *stream);
+                                float *logits, float *act, int32_t *pick, float min_prob, int fallback,
+                                void *stream);
 RT_API rt_status rt_mlp_backward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x,
                                  const float *act, const float *logits, const int32_t *label, int B,
                                  float *grad, float *loss, void *stream);
@@ -372,14 +377,20 @@ RT_API rt_status rt_mlp_adamw(rt_ctx *ctx, float *master, uint16_t *wb, const fl
  */
 RT_API rt_status rt_set_picker(rt_ctx *ctx, const uint16_t *wb, const float *norm);
 
-/* Variants (RT_RASTER..RT_HYBRID) the picker chose for the tiles of the last
- * chunk (up to 32 tiles) of the last learned rt_segment_batch call; copies up
- * to cap of them into variants (nullable) and returns how many there were.
- * The choices stay on the device during the call (the propagation reads
- * them there) and are copied to pinned host memory at its end; this call
- * waits for that copy. After the replay of a captured graph the caller
+/* The picker's three schedules on this context: class c runs variants[c]
+ * (RT_AUTO = RT_RASTER) with max_locals[c] sweep iterations per dense tile
+ * visit (0 = the variant's default). Default: RT_RASTER with 4, 12, 24. */
+RT_API rt_status rt_set_picker_classes(rt_ctx *ctx, const int *variants, const int *max_locals);
+
+/* Classes the picker chose for the tiles of the last chunk (up to 32 tiles)
+ * of the last learned rt_segment_batch call: 0..2, or 3 where the pick fell
+ * back to the call's plain schedule (confidence below pick_min_prob). Copies
+ * up to cap of them into classes (nullable) and returns how many there
+ * were. The choices stay on the device during the call (the propagation
+ * reads them there) and are copied to pinned host memory at its end; this
+ * call waits for that copy. After the replay of a captured graph the caller
  * synchronizes the stream first. Returns 0 on a CUDA error. */
-RT_API int rt_last_picks(const rt_ctx *ctx, int *variants, int cap);
+RT_API int rt_last_picks(const rt_ctx *ctx, int *classes, int cap);
 
 /* One tile of a batch. Every pointer is a device pointer. */
 typedef struct {
@@ -407,13 +418,17 @@ typedef struct {
     int conn_recon;  /* connectivity of the reconstruction (8) */
     int conn_fill;   /* connectivity of the background flood in fill-holes (4) */
     int variant;     /* reconstruction variant for every tile (RT_AUTO) */
-    int max_local;   /* sweep iterations per dense tile visit; 0 = default */
-    int policy;      /* RT_POLICY_PLAIN: `variant` for every tile;
-                        RT_POLICY_LEARNED: the attached picker chooses per tile and the
-                        plain choice is kept whenever no picker is attached */
+    int max_local;   /* sweep iterations per dense tile visit; 0 = default (12; RT_HYBRID 64) */
+    int policy;      /* RT_POLICY_PLAIN: `variant` and `max_local` for every tile;
+                        RT_POLICY_LEARNED: the attached picker chooses a schedule per tile
+                        (rt_set_picker_classes), and the plain schedule is kept whenever no
+                        picker is attached */
     int max_iters;   /* tile visits per 32 x 64 tile allowed to the propagation, as in
                         rt_set_limits; 0 = the context's bound */
     int timeout_ms;  /* device-time bound of each propagation; 0 = the context's (20 s) */
+    int pick_min_prob; /* learned policy: the network's pick stands only when its softmax
+                          probability is at least pick_min_prob / 1000; below, the tile runs
+                          the plain schedule (`variant`, `max_local`). 0 = always the pick */
 } rt_seg_params;
 
 enum { RT_POLICY_PLAIN = 0, RT_POLICY_LEARNED = 1 };

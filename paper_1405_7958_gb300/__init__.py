@@ -312,14 +312,17 @@ class Picker:
                "rt_feature_norm")
         self.norm = norm
 
-    def forward(self, x: torch.Tensor, with_act: bool = False, stream=None):
+    def forward(self, x: torch.Tensor, with_act: bool = False, min_prob: float = 0.0, fallback: int = 3,
+                stream=None):
+        """Logits, saved activations (with_act) and picks; a pick whose
+        softmax probability is below min_prob becomes `fallback`."""
         B = x.shape[0]
         logits = torch.empty((B, 3), dtype=torch.float32, device=self.device)
         act = torch.empty((B, 128), dtype=torch.float32, device=self.device) if with_act else None
         pick = torch.empty(B, dtype=torch.int32, device=self.device)
         _check(lib().rt_mlp_forward(self.ctx.handle, self.wb.data_ptr(), self.norm.data_ptr(), x.contiguous().data_ptr(),
                                     B, logits.data_ptr(), None if act is None else act.data_ptr(), pick.data_ptr(),
-                                    _stream(stream)), "rt_mlp_forward")
+                                    float(min_prob), int(fallback), _stream(stream)), "rt_mlp_forward")
         return logits, act, pick
 
     def backward(self, x, act, logits, label, stream=None):
@@ -350,7 +353,20 @@ class Picker:
         self.step_count = int(sd["step_count"])
 
 
+PICKER_CLASSES = ((RT_RASTER, 4), (RT_RASTER, 12), (RT_RASTER, 24))   # the library's default table
+
+
+def set_picker_classes(classes, ctx=None):
+    """The picker's three schedules on ctx: ((variant, max_local), ...)."""
+    ctx = ctx or default_context()
+    v = (ctypes.c_int * 3)(*[int(c[0]) for c in classes])
+    m = (ctypes.c_int * 3)(*[int(c[1]) for c in classes])
+    _check(lib().rt_set_picker_classes(ctx.handle, v, m), "rt_set_picker_classes")
+
+
 def last_picks(ctx=None) -> list:
+    """Classes (0..2, or 3 = fell back to the plain schedule) the picker
+    chose for the tiles of the last learned chunk."""
     ctx = ctx or default_context()
     buf = (ctypes.c_int * 32)()
     n = lib().rt_last_picks(ctx.handle, buf, 32)
@@ -370,6 +386,7 @@ class SegParams:
     policy: int = 0          # 0 plain (fixed variant), 1 learned (attached picker)
     max_iters: int = 0       # tile visits per tile allowed to the propagation (0: the context's bound)
     timeout_ms: int = 0      # device-time bound of each propagation (0: the context's)
+    pick_min_prob: int = 0   # learned: a pick stands only at softmax probability >= this / 1000
 
     def to_c(self) -> _native.RtSegParams:
         p = _native.RtSegParams()

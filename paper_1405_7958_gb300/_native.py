@@ -20,7 +20,7 @@ EXPORTS = (
     "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_recon_stats",
     "rt_edt_noalloc", "rt_synth_tile", "rt_tile_features", "rt_mlp_forward", "rt_mlp_backward",
     "rt_mlp_adamw", "rt_set_picker", "rt_last_picks", "rt_set_limits", "rt_segment_workspace_bytes",
-    "rt_feature_norm", "rt_watershed", "rt_object_features",
+    "rt_feature_norm", "rt_watershed", "rt_object_features", "rt_set_picker_classes",
 )
 RT_NPHASES = 9
 PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt", "pick", "objects", "watershed")
@@ -48,7 +48,8 @@ class RtTile(ctypes.Structure):
 
 class RtSegParams(ctypes.Structure):
     _fields_ = [(n, _int) for n in ("h_offset", "threshold", "min_area", "max_area", "conn_recon",
-                                    "conn_fill", "variant", "max_local", "policy", "max_iters", "timeout_ms")]
+                                    "conn_fill", "variant", "max_local", "policy", "max_iters", "timeout_ms",
+                                    "pick_min_prob")]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -88,7 +89,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_tile_features.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_int),
                                      ctypes.POINTER(_int), _int, _vp, _vp]
     lib.rt_tile_features.restype = _int
-    lib.rt_mlp_forward.argtypes = [_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp]
+    lib.rt_mlp_forward.argtypes = [_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, ctypes.c_float, _int, _vp]
     lib.rt_mlp_forward.restype = _int
     lib.rt_mlp_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp]
     lib.rt_mlp_backward.restype = _int
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_mlp_adamw.restype = _int
     lib.rt_set_picker.argtypes = [_vp, _vp, _vp]
     lib.rt_set_picker.restype = _int
+    lib.rt_set_picker_classes.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int)]
+    lib.rt_set_picker_classes.restype = _int
     lib.rt_last_picks.argtypes = [_vp, ctypes.POINTER(_int), _int]
     lib.rt_last_picks.restype = _int
     lib.rt_seg_params_default.argtypes = [ctypes.POINTER(RtSegParams)]

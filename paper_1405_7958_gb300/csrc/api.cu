@@ -37,6 +37,7 @@ struct rt_ctx {
     cudaEvent_t picks_ev = nullptr;        // recorded after their copy (not under stream capture)
     bool picks_ev_valid = false;
     int n_last_picks = 0;
+    PickTable classes{{0, 0, 0, 0}, {4, 12, 24, 12}};   // picker classes (rt_set_picker_classes); entry 3 per call
     int max_iters = 0;                     // limits of the single-operation entry points (rt_set_limits)
     uint64_t timeout_ns = 0;
     std::vector<PhaseRec> recs;
@@ -186,10 +187,17 @@ struct Limits {
 
 Limits ctx_limits(const rt_ctx *ctx) { return {ctx->max_iters, ctx->timeout_ns ? ctx->timeout_ns : kSweepTimeoutNs}; }
 
+int default_max_local(int variant) { return variant == RT_HYBRID ? 64 : 12; }
+
 rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int variant, int max_local, int32_t *err,
                     cudaStream_t s, Limits lim, const int32_t *pick = nullptr)
 {
     if (variant == RT_AUTO) variant = RT_RASTER;
+    // the learned policy's schedules: the picker's classes, then the call's
+    // plain schedule as the fall-back entry
+    PickTable table = ctx->classes;
+    table.group[kPickClasses] = variant - RT_RASTER;
+    table.max_local[kPickClasses] = max_local > 0 ? max_local : default_max_local(variant);
     // RT_RASTER / RT_QUEUE: every tile starts flagged for a dense visit (the
     // queue visit then seeds every pixel); RT_HYBRID: nothing flagged, the
     // dense pass over all tiles flags what remains.
@@ -197,7 +205,7 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
     RT_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, kCtlWords * sizeof(uint32_t), s));
     {
         Phase ph(ctx, RT_PHASE_RECON_INIT, s);
-        RT_CUDA_TRY(launch_recon_init(b, w.flags, w.ctl, flag0, pick, w.map, err, s));
+        RT_CUDA_TRY(launch_recon_init(b, w.flags, w.ctl, flag0, pick, table, w.map, err, s));
         ctx->launches += 1;
     }
     ctx->visits_dev = w.ctl + kCtlVisits;
@@ -215,16 +223,22 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
     p.abort = w.ctl + kCtlAbort;
     p.map = nullptr;
     p.nvirt = nullptr;
+    p.pick = pick;
+    p.table = table;
     int grid = 0;
     Phase ph(ctx, RT_PHASE_RECON_SWEEP, s);
+    bool used[kGroups] = {false, false, false};   // groups some schedule of the table propagates in
+    for (int e = 0; e < kPickEntries; ++e)
+        if (table.group[e] >= 0 && table.group[e] < kGroups) used[table.group[e]] = true;
     for (int g = 0; g < (pick ? kGroups : 1); ++g) {
+        if (pick && !used[g]) continue;
         const int v = pick ? RT_RASTER + g : variant;
         if (pick) {
             p.map = w.map + (size_t)g * b.ntiles;
             p.nvirt = w.ctl + kCtlGroupCount + g;
             p.pending = w.ctl + kCtlGroupPending + g;
         }
-        p.max_local = max_local > 0 ? max_local : (v == RT_HYBRID ? 64 : 12);
+        p.max_local = max_local > 0 ? max_local : default_max_local(v);
         if (v == RT_HYBRID) {
             RT_CUDA_TRY(launch_recon_dense(p, conn, s));
             ctx->launches += 1;
@@ -270,6 +284,7 @@ bool bad_params(const rt_seg_params &P)
     if (P.variant < RT_AUTO || P.variant > RT_HYBRID) return true;
     if (P.policy != RT_POLICY_PLAIN && P.policy != RT_POLICY_LEARNED) return true;
     if (P.max_local < 0 || P.max_iters < 0 || P.timeout_ms < 0) return true;
+    if (P.pick_min_prob < 0 || P.pick_min_prob > 1000) return true;
     return false;
 }
 
@@ -812,12 +827,26 @@ rt_status rt_tile_features(rt_ctx *ctx, const uint8_t *const *imgs, const int64_
 }
 
 rt_status rt_mlp_forward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, int B, float *logits,
-                         float *act, int32_t *pick, void *stream)
+                         float *act, int32_t *pick, float min_prob, int fallback, void *stream)
 {
-    if (!ctx || !wb || !norm || !x || B < 1) return RT_EINVAL;
+    if (!ctx || !wb || !norm || !x || B < 1 || !(min_prob <= 1.0f) || fallback < 0) return RT_EINVAL;
     DeviceGuard g(ctx->device);
     ctx->launches += 1;
-    return cuda_status(launch_mlp_forward(wb, norm, x, B, logits, act, pick, (cudaStream_t)stream));
+    return cuda_status(launch_mlp_forward(wb, norm, x, B, logits, act, pick, min_prob, fallback, (cudaStream_t)stream));
+}
+
+rt_status rt_set_picker_classes(rt_ctx *ctx, const int *variants, const int *max_locals)
+{
+    if (!ctx || !variants || !max_locals) return RT_EINVAL;
+    PickTable t = ctx->classes;
+    for (int c = 0; c < kPickClasses; ++c) {
+        const int v = variants[c] == RT_AUTO ? RT_RASTER : variants[c];
+        if (v < RT_RASTER || v > RT_HYBRID || max_locals[c] < 0) return RT_EINVAL;
+        t.group[c] = v - RT_RASTER;
+        t.max_local[c] = max_locals[c] > 0 ? max_locals[c] : default_max_local(v);
+    }
+    ctx->classes = t;
+    return RT_OK;
 }
 
 rt_status rt_mlp_backward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, const float *act,
@@ -850,7 +879,7 @@ rt_status rt_mlp_adamw(rt_ctx *ctx, float *master, uint16_t *wb, const float *gr
         launch_mlp_adamw(master, wb, grad, m, v, step, lr, beta1, beta2, eps, weight_decay, (cudaStream_t)stream));
 }
 
-int rt_last_picks(const rt_ctx *ctx, int *variants, int cap)
+int rt_last_picks(const rt_ctx *ctx, int *classes, int cap)
 {
     if (!ctx) return 0;
     if (ctx->picks_ev_valid) {
@@ -861,9 +890,9 @@ int rt_last_picks(const rt_ctx *ctx, int *variants, int cap)
         }
     }
     const int n = ctx->n_last_picks < cap ? ctx->n_last_picks : cap;
-    for (int i = 0; variants && i < n; ++i) {
-        const int g = ctx->picks_host[i];
-        variants[i] = (g >= 0 && g < kGroups) ? RT_RASTER + g : RT_RASTER;
+    for (int i = 0; classes && i < n; ++i) {
+        const int c = ctx->picks_host[i];
+        classes[i] = (c >= 0 && c < kPickClasses) ? c : kPickClasses;
     }
     return ctx->n_last_picks;
 }
@@ -890,6 +919,7 @@ void rt_seg_params_default(rt_seg_params *p)
     p->policy = RT_POLICY_PLAIN;
     p->max_iters = 0;
     p->timeout_ms = 0;
+    p->pick_min_prob = 0;
 }
 
 rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_seg_params *params, void *stream)
@@ -926,7 +956,8 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
             {
                 Phase ph(ctx, RT_PHASE_PICK, s);
                 RT_CUDA_TRY(launch_features(c.fb, c.feat, s));
-                RT_CUDA_TRY(launch_mlp_forward(ctx->picker_wb, ctx->picker_norm, c.feat, cn, nullptr, nullptr, c.picks, s));
+                RT_CUDA_TRY(launch_mlp_forward(ctx->picker_wb, ctx->picker_norm, c.feat, cn, nullptr, nullptr, c.picks,
+                                               (float)P.pick_min_prob / 1000.0f, kPickClasses, s));
                 ctx->launches += 5;
             }
             st = run_recon(ctx, c.b, c.w, P.conn_recon, P.variant, P.max_local, c.w.err, s, lim, c.picks);

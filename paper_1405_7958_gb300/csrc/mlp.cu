@@ -22,7 +22,8 @@ __device__ __forceinline__ float bf(uint16_t h)
 
 // one thread per sample; parameters staged in shared memory as fp32
 __global__ void __launch_bounds__(256) mlp_forward_kernel(const uint16_t *wb, const float *norm, const float *x, int B,
-                                                          float *logits, float *act, int32_t *pick)
+                                                          float *logits, float *act, int32_t *pick, float min_prob,
+                                                          int fallback)
 {
     __shared__ float P[kMlpParams];
     __shared__ float mu[kMlpIn], sd[kMlpIn];
@@ -66,6 +67,14 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(const uint16_t *wb, co
     for (int k = 0; k < kMlpOut; ++k) {
         if (logits) logits[(int64_t)b * kMlpOut + k] = z[k];
         if (z[k] > z[best]) best = k;
+    }
+    // confidence fall-back: the pick stands only when its softmax
+    // probability 1 / sum_k exp(z_k - z_best) reaches min_prob
+    if (min_prob > 0.f) {
+        float se = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMlpOut; ++k) se += expf(z[k] - z[best]);
+        if (1.f / se < min_prob) best = fallback;
     }
     if (pick) pick[b] = best;
 }
@@ -168,10 +177,11 @@ __global__ void mlp_adamw_kernel(float *master, uint16_t *wb, const float *grad,
 }
 
 cudaError_t launch_mlp_forward(const uint16_t *wb, const float *norm, const float *x, int B, float *logits, float *act,
-                               int32_t *pick, cudaStream_t s)
+                               int32_t *pick, float min_prob, int fallback, cudaStream_t s)
 {
     if (B <= 0) return cudaSuccess;
-    mlp_forward_kernel<<<(unsigned)ceil_div(B, 256), 256, 0, s>>>(wb, norm, x, B, logits, act, pick);
+    mlp_forward_kernel<<<(unsigned)ceil_div(B, 256), 256, 0, s>>>(wb, norm, x, B, logits, act, pick, min_prob,
+                                                                  fallback);
     return cudaGetLastError();
 }
 

@@ -17,8 +17,10 @@ constexpr int kMlpParams = kB3 + kMlpOut;                 // 5955
 constexpr int kMlpAct = 2 * kMlpH;                        // saved h1, h2 per sample
 constexpr int kMlpDelta = kMlpOut + 2 * kMlpH + kMlpIn + 1;   // dz, dh2, dh1, xn, loss per sample
 
+// pick = argmax of the logits, or `fallback` where the argmax's softmax
+// probability is below min_prob (min_prob <= 0: never)
 cudaError_t launch_mlp_forward(const uint16_t *wb, const float *norm, const float *x, int B, float *logits, float *act,
-                               int32_t *pick, cudaStream_t s);
+                               int32_t *pick, float min_prob, int fallback, cudaStream_t s);
 size_t mlp_backward_workspace_bytes(int B);
 cudaError_t launch_mlp_backward(const uint16_t *wb, const float *norm, const float *x, const float *act,
                                 const float *logits, const int32_t *label, int B, float *grad, float *loss, float *ws,

@@ -35,9 +35,14 @@ constexpr int kWarpWords = 2 * kTH * kTS + 2 * (kTH + 2) + kTH * 32 / 2;
 
 // ---------------------------------------------------------------- init
 // Iw = mask (0 in the padding), Rw = min(J, I). One thread per 4 pixels.
-__device__ __forceinline__ int pick_group(const int32_t *pick, int i)
+__device__ __forceinline__ int pick_entry(const int32_t *pick, int i)
 {
-    const int g = pick[i];
+    const int c = pick[i];
+    return (c >= 0 && c < kPickEntries) ? c : kPickClasses;
+}
+__device__ __forceinline__ int pick_group(const int32_t *pick, const PickTable &t, int i)
+{
+    const int g = t.group[pick_entry(pick, i)];
     return (g >= 0 && g < kGroups) ? g : 0;
 }
 
@@ -65,7 +70,7 @@ __device__ __forceinline__ uint4 load16(const uint8_t *p, int n)
 // Iw = mask (0 in the padding), Rw = min(J, I); blocks of row 0 also set the
 // image's tile flags (and queue nothing: the propagation starts from them).
 __global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
-                                  const int32_t *pick, int32_t *map, int32_t *err)
+                                  const int32_t *pick, const PickTable table, int32_t *map, int32_t *err)
 {
     const int i = blockIdx.z;
     const ReconImage &d = b.img[i];
@@ -76,10 +81,10 @@ __global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t 
             for (int k = tid; k < nt; k += nth) flags[d.tile_base + k] = flag0;
             if (i == 0 && tid == 0) ctl[kCtlPending] = flag0 ? (uint32_t)b.ntiles : 0u;
         } else {
-            const int g = pick_group(pick, i);
+            const int g = pick_group(pick, table, i);
             int off = 0;   // tiles of group g in the images before this one
             for (int j = 0; j < i; ++j)
-                if (pick_group(pick, j) == g) off += b.img[j].tiles_x * b.img[j].tiles_y;
+                if (pick_group(pick, table, j) == g) off += b.img[j].tiles_x * b.img[j].tiles_y;
             int32_t *mg = map + (int64_t)g * b.ntiles + off;
             const uint32_t f0 = g == 2 ? 0u : 2u;
             for (int k = tid; k < nt; k += nth) {
@@ -88,7 +93,7 @@ __global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t 
             }
             if (i == 0 && tid == 0) {
                 uint32_t cnt[kGroups] = {0u, 0u, 0u};
-                for (int j = 0; j < b.n; ++j) cnt[pick_group(pick, j)] += b.img[j].tiles_x * b.img[j].tiles_y;
+                for (int j = 0; j < b.n; ++j) cnt[pick_group(pick, table, j)] += b.img[j].tiles_x * b.img[j].tiles_y;
                 for (int q = 0; q < kGroups; ++q) {
                     ctl[kCtlGroupCount + q] = cnt[q];
                     ctl[kCtlGroupPending + q] = q == 2 ? 0u : cnt[q];
@@ -140,7 +145,8 @@ __global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t 
 }
 
 cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
-                              const int32_t *pick, int32_t *map, int32_t *err, cudaStream_t s)
+                              const int32_t *pick, const PickTable &table, int32_t *map, int32_t *err,
+                              cudaStream_t s)
 {
     if (pick && !map) return cudaErrorInvalidValue;
     int maxHp = 1, maxWp = 16;
@@ -150,7 +156,7 @@ cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *ct
     }
     const int threads = 128;
     const dim3 grid((unsigned)ceil_div(maxWp / 16, threads), (unsigned)maxHp, (unsigned)b.n);
-    recon_init_kernel<<<grid, threads, 0, s>>>(b, flags, ctl, flag0, pick, map, err);
+    recon_init_kernel<<<grid, threads, 0, s>>>(b, flags, ctl, flag0, pick, table, map, err);
     return cudaGetLastError();
 }
 
@@ -244,11 +250,17 @@ __device__ __forceinline__ void mark_neighbours(const SweepParams &p, const Reco
     if (stale) atomicSub(p.pending, stale);
 }
 
-__device__ __forceinline__ const ReconImage &find_image(const SweepParams &p, int t)
+__device__ __forceinline__ int find_image(const SweepParams &p, int t)
 {
     int k = 0;
     while (k + 1 < p.b.n && t >= p.b.img[k + 1].tile_base) ++k;
-    return p.b.img[k];
+    return k;
+}
+
+// sweep iterations a dense visit of image k may make before it is revisited
+__device__ __forceinline__ int visit_budget(const SweepParams &p, int k)
+{
+    return p.pick ? p.table.max_local[pick_entry(p.pick, k)] : p.max_local;
 }
 
 // Halo columns of tile (tx, ty) from the neighbours' edge columns: hl for
@@ -283,7 +295,9 @@ struct WarpBuf {
 template <int CONN>
 __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, const WarpBuf &wb, int lane)
 {
-    const ReconImage &d = find_image(p, t);
+    const int img = find_image(p, t);
+    const ReconImage &d = p.b.img[img];
+    const int max_local = visit_budget(p, img);
     const int lt = t - d.tile_base;          // column-major: lt = tx * tiles_y + ty
     const int ty = lt % d.tiles_y, tx = lt / d.tiles_y;
     const int r0 = ty * kTH, c0 = tx * kTW;
@@ -317,7 +331,7 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
     bool converged = false;
     int it = 0;
     int clean = 0;          // consecutive passes without a change
-    for (; it < p.max_local && !converged; ++it) {
+    for (; it < max_local && !converged; ++it) {
         bool ch = false;
         // down sweep
         uint32_t prev = topw;
@@ -490,7 +504,7 @@ __device__ __forceinline__ void q_relax(const QBuf &qb, int r, int c, uint32_t v
 template <int CONN>
 __device__ __forceinline__ uint32_t visit_queue(const SweepParams &p, int t, uint32_t bits, const QBuf &qb, int lane)
 {
-    const ReconImage &d = find_image(p, t);
+    const ReconImage &d = p.b.img[find_image(p, t)];
     const int lt = t - d.tile_base;
     const int ty = lt % d.tiles_y, tx = lt / d.tiles_y;
     const int r0 = ty * kTH, c0 = tx * kTW;

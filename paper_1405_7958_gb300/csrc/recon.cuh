@@ -45,6 +45,17 @@ struct ReconBatch {
     ReconImage img[kMaxImgs];
 };
 
+// Schedules the picker chooses between: entry c (c < kPickClasses) is class
+// c of the network, entry kPickClasses the plain schedule of the call (the
+// fall-back). group = variant - 1 (0 raster, 1 queue, 2 hybrid); max_local =
+// that schedule's sweep iterations per dense visit.
+constexpr int kPickClasses = 3;
+constexpr int kPickEntries = kPickClasses + 1;
+struct PickTable {
+    int group[kPickEntries];
+    int max_local[kPickEntries];
+};
+
 struct SweepParams {
     ReconBatch b;
     int ntiles;
@@ -59,6 +70,8 @@ struct SweepParams {
     uint32_t *abort;          // nonzero: a bound was reached, every warp leaves
     const int32_t *map;       // NULL: the launch covers tiles 0..ntiles-1; else its k-th tile is map[k]
     const uint32_t *nvirt;    // with map: number of tiles the launch covers (device word)
+    const int32_t *pick;      // NULL: max_local for every tile; else image i runs table.max_local of pick[i]
+    PickTable table;
 };
 
 // Control words of a propagation (device, zeroed before the init kernel):
@@ -78,12 +91,14 @@ void plan_recon_image(ReconImage &d, int H, int W);
 cudaError_t launch_marker(const uint8_t *mask, int64_t ld_mask, uint8_t *marker, int64_t ld_marker, int H,
                           int W, int h_offset, cudaStream_t s);
 // pick == NULL: every tile starts with flag0, ctl[kCtlPending] counts them.
-// pick != NULL (device, one entry per image, 0 raster / 1 queue / 2 hybrid,
-// anything else raster): tiles of raster and queue images start flagged,
-// hybrid ones not; map[g * ntiles + k] lists the tiles of group g in batch
-// order, with their count and pending count in ctl.
+// pick != NULL (device, one table entry per image; out-of-range entries are
+// the plain schedule): an image propagates in group table.group[entry];
+// tiles of raster and queue images start flagged, hybrid ones not;
+// map[g * ntiles + k] lists the tiles of group g in batch order, with their
+// count and pending count in ctl.
 cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
-                              const int32_t *pick, int32_t *map, int32_t *err, cudaStream_t s);
+                              const int32_t *pick, const PickTable &table, int32_t *map, int32_t *err,
+                              cudaStream_t s);
 // one dense visit of every tile (non-persistent)
 cudaError_t launch_recon_dense(const SweepParams &p, int conn, cudaStream_t s);
 // persistent visits of flagged tiles until quiescence; queue = 1: queue visits

@@ -1,14 +1,22 @@
-"""Training and evaluation of the learned variant picker.
+"""Training and evaluation of the learned schedule picker.
 
-The picker chooses, per tile, how its reconstruction propagates (RT_RASTER,
-RT_QUEUE or RT_HYBRID; all three give identical bytes). Its training data
-are timings the method itself produces: every tile is drawn on the GPU,
-reconstructed with each variant (CUDA events on the launch stream, median of
-`reps` runs), and checked to give the same output under all three; the
-label is the fastest variant. Training runs the library's own forward,
-backward and AdamW kernels; torch only holds the buffers.
+The picker chooses, per tile, how its reconstruction propagates: one of three
+schedules (a variant and its sweep iterations per dense tile visit; by
+default the raster sweeps with 4, 12 and 24 iterations), all giving
+identical bytes. Its training data are timings the method itself produces:
+every tile is drawn on the GPU, segmented with each schedule (CUDA events on
+the launch stream, median of `reps` runs), and checked to give the same
+labels and distances under all three; the label is the fastest schedule.
+Training runs the library's own forward, backward, AdamW and normalisation
+kernels; torch only holds the buffers.
 
-    python -m paper_1405_7958_gb300.picker --train 4000 --eval 512 \
+The robustness study (the paper's PATS evaluation perturbs the speedup
+estimates its scheduler relies on, Section 5.5) adds Gaussian noise of
+sigma feature standard deviations to the held-out features and reports,
+with and without the confidence fall-back to the plain schedule, what the
+picks cost against the plain schedule.
+
+    python -m paper_1405_7958_gb300.picker --train 20000 --eval 512 \
         --out picker.npz --report picker_report.json
 """
 from __future__ import annotations
@@ -23,8 +31,9 @@ import torch
 
 import paper_1405_7958_gb300 as rt
 
-VARIANTS = (rt.RT_RASTER, rt.RT_QUEUE, rt.RT_HYBRID)
-NAMES = ("raster", "queue", "hybrid")
+SCHEDULES = rt.PICKER_CLASSES            # class c runs SCHEDULES[c] = (variant, max_local)
+NAMES = tuple(f"raster/{m}" if v == rt.RT_RASTER else f"{v}/{m}" for v, m in SCHEDULES)
+PLAIN = 1                                # the plain schedule (RT_RASTER, 12) is class 1
 
 
 def tile_specs(n: int, seed: int, lo: int = 1024, hi: int = 4096, step: int = 256):
@@ -34,30 +43,31 @@ def tile_specs(n: int, seed: int, lo: int = 1024, hi: int = 4096, step: int = 25
     return synth.batch_sizes(n, seed, lo, hi, step)
 
 
-def variant_times(ctx, img: torch.Tensor, reps: int = 3, stream=None):
-    """Median reconstruction time (ms) of each variant on one tile, and
-    whether all variants produced the same bytes."""
+def schedule_times(ctx, img: torch.Tensor, reps: int = 3, stream=None):
+    """Median chain time (ms) of each schedule on one tile, and whether all
+    schedules produced the same labels and distances."""
     stream = stream or torch.cuda.current_stream()
     outs, times = [], []
-    for v in VARIANTS:
-        out = torch.empty_like(img)
+    for v, m in SCHEDULES:
+        p = rt.SegParams(variant=v, max_local=m)
+        o = rt.segment_batch([img], p, ctx=ctx, stream=stream, want_recon=False, want_filled=False)
         ts = []
         for _ in range(reps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            rt.reconstruct(img, None, h_offset=30, conn=8, variant=v, out=out, ctx=ctx, stream=stream)
+            rt.segment_batch([img], p, outputs=o, ctx=ctx, stream=stream, want_recon=False, want_filled=False)
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
         times.append(float(np.median(ts)))
-        outs.append(out)
-    same = all(torch.equal(outs[0], o) for o in outs[1:])
+        outs.append(o[0])
+    same = all(torch.equal(outs[0]["L"], o["L"]) and torch.equal(outs[0]["D"], o["D"]) for o in outs[1:])
     return times, same
 
 
 def build_dataset(n: int, seed: int, reps: int = 3, ctx=None, log_every: int = 500, cache: str | None = None):
-    """Features (n x 24) and variant times (n x 3, ms) of n GPU-drawn tiles.
+    """Features (n x 24) and schedule times (n x 3, ms) of n GPU-drawn tiles.
     With `cache`, finished rows are saved and a rerun resumes from them."""
     ctx = ctx or rt.Context()
     specs = tile_specs(n, seed)
@@ -69,17 +79,17 @@ def build_dataset(n: int, seed: int, reps: int = 3, ctx=None, log_every: int = 5
         k = int(z["done"])
         if z["feats"].shape[0] == n:
             feats[:k], times[:k], start = z["feats"][:k], z["times"][:k], k
-    # one warm-up of every variant
+    # one warm-up of every schedule
     warm = rt.synth_tile(1024, 1024, 1, 40, ctx=ctx)
-    variant_times(ctx, warm, 1)
+    schedule_times(ctx, warm, 1)
     t0 = time.time()
     for i in range(start, n):
         H, W, ns, s = specs[i]
         img = rt.synth_tile(H, W, s, ns, ctx=ctx)
         feats[i] = rt.tile_features([img], ctx=ctx).cpu().numpy()[0]
-        tv, same = variant_times(ctx, img, reps)
+        tv, same = schedule_times(ctx, img, reps)
         if not same:
-            raise RuntimeError(f"variants disagree on tile {i} (seed {s})")
+            raise RuntimeError(f"schedules disagree on tile {i} (seed {s})")
         times[i] = tv
         if log_every and (i + 1) % log_every == 0:
             print(f"  dataset {i + 1}/{n}  {time.time() - t0:.0f} s", flush=True)
@@ -111,26 +121,65 @@ def train(feats: np.ndarray, times: np.ndarray, epochs: int = 60, batch: int = 2
     return pk
 
 
-def evaluate(pk: rt.Picker, feats: np.ndarray, times: np.ndarray) -> dict:
-    """Selection accuracy, regret, and the summed reconstruction time of the
-    picks against the plain schedule (RT_RASTER for every tile) and against
-    the best variant per tile."""
-    x = torch.from_numpy(np.ascontiguousarray(feats)).to(pk.device)
-    _, _, pick = pk.forward(x)
-    pick = pick.cpu().numpy()
+def choose(pk: rt.Picker, feats: np.ndarray, min_prob: float = 0.0) -> np.ndarray:
+    """The picker's classes for these features (class 3: fell back to the
+    plain schedule), from the library's forward kernel."""
+    x = torch.from_numpy(np.ascontiguousarray(feats, dtype=np.float32)).to(pk.device)
+    _, _, pick = pk.forward(x, min_prob=min_prob, fallback=3)
+    return pick.cpu().numpy()
+
+
+def cost(times: np.ndarray, pick: np.ndarray) -> np.ndarray:
+    """Per-tile time of the picks (a fall-back runs the plain schedule)."""
+    cls = np.where(pick < len(SCHEDULES), pick, PLAIN)
+    return times[np.arange(len(times)), cls]
+
+
+def evaluate(pk: rt.Picker, feats: np.ndarray, times: np.ndarray, min_prob: float = 0.0) -> dict:
+    """Selection accuracy, regret, and the summed time of the picks against
+    the plain schedule for every tile and against the best schedule per
+    tile."""
+    pick = choose(pk, feats, min_prob)
     best = times.argmin(axis=1)
-    chosen = times[np.arange(len(times)), pick]
+    chosen = cost(times, pick)
     return {
         "tiles": int(len(times)),
         "accuracy": float((pick == best).mean()),
-        "pick_counts": {NAMES[k]: int((pick == k).sum()) for k in range(3)},
-        "best_counts": {NAMES[k]: int((best == k).sum()) for k in range(3)},
+        "pick_counts": {NAMES[k]: int((pick == k).sum()) for k in range(len(SCHEDULES))} | {
+            "fell_back": int((pick >= len(SCHEDULES)).sum())},
+        "best_counts": {NAMES[k]: int((best == k).sum()) for k in range(len(SCHEDULES))},
         "regret_mean_ms": float((chosen - times.min(axis=1)).mean()),
         "time_learned_ms": float(chosen.sum()),
-        "time_plain_ms": float(times[:, 0].sum()),
+        "time_plain_ms": float(times[:, PLAIN].sum()),
         "time_best_ms": float(times.min(axis=1).sum()),
-        "gain_vs_plain": float(times[:, 0].sum() / chosen.sum()),
+        "time_worst_ms": float(times.max(axis=1).sum()),
+        "gain_vs_plain": float(times[:, PLAIN].sum() / chosen.sum()),
     }
+
+
+def robustness(pk: rt.Picker, feats: np.ndarray, times: np.ndarray, sigmas=(0.0, 0.5, 1.0, 2.0, 4.0),
+               min_probs=(0.0, 0.6, 0.8, 0.95), seed: int = 7, repeats: int = 5) -> list:
+    """Estimate-error study: Gaussian noise of sigma feature standard
+    deviations on the inputs (`repeats` draws), picks with and without the
+    confidence fall-back; what they cost against the plain schedule (> 1:
+    slower than plain) and how often the picker fell back."""
+    rng = np.random.default_rng(seed)
+    sd = pk.norm[24:].cpu().numpy().astype(np.float64)
+    plain = times[:, PLAIN].sum()
+    rows = []
+    for sg in sigmas:
+        draws = [feats + sg * sd * rng.standard_normal(feats.shape) for _ in range(repeats if sg > 0 else 1)]
+        for mp in min_probs:
+            ratios, fb = [], []
+            for x in draws:
+                pick = choose(pk, x.astype(np.float32), mp)
+                ratios.append(float(cost(times, pick).sum() / plain))
+                fb.append(float((pick >= len(SCHEDULES)).mean()))
+            rows.append({"sigma": sg, "min_prob": mp, "time_vs_plain": float(np.mean(ratios)),
+                         "time_vs_plain_max": float(np.max(ratios)), "fell_back": float(np.mean(fb))})
+    rows.append({"bounds": {"best_vs_plain": float(times.min(axis=1).sum() / plain),
+                            "worst_vs_plain": float(times.max(axis=1).sum() / plain)}})
+    return rows
 
 
 def save(pk: rt.Picker, path: str):
@@ -148,7 +197,7 @@ def load(path: str, device=None) -> rt.Picker:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=4000)
+    ap.add_argument("--train", type=int, default=20000)
     ap.add_argument("--eval", type=int, default=512)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--epochs", type=int, default=60)
@@ -166,8 +215,11 @@ def main():
     t1 = time.time()
     pk = train(ftr, ttr, epochs=a.epochs, seed=a.seed)
     t2 = time.time()
-    rep = {"train": evaluate(pk, ftr, ttr), "eval": evaluate(pk, fev, tev),
+    rep = {"schedules": [{"class": k, "variant": v, "max_local": m} for k, (v, m) in enumerate(SCHEDULES)],
+           "plain_class": PLAIN, "train": evaluate(pk, ftr, ttr), "eval": evaluate(pk, fev, tev),
+           "robustness_eval": robustness(pk, fev, tev),
            "dataset_s": t1 - t0, "train_s": t2 - t1, "epochs": a.epochs, "reps": a.reps}
+    np.savez(os.path.splitext(a.report)[0] + "_eval_set.npz", feats=fev, times=tev)
     save(pk, a.out)
     with open(a.report, "w") as fh:
         json.dump(rep, fh, indent=1)

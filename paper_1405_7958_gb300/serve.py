@@ -179,7 +179,7 @@ def run_batched(reqs, pool, budget_bytes: int = 40 << 30, max_batch: int = 32, n
     attached picker chooses each tile's variant)."""
     hp = hp or PinnedPool()
     streams = [torch.cuda.Stream() for _ in range(n_streams)]
-    params = rt.SegParams(policy=policy)
+    params = rt.SegParams(policy=policy, pick_min_prob=600 if policy else 0)   # learned: with the fall-back
     reserve = rt.segment_workspace_bytes([(4096, 4096)] * BATCH_TILES_4K, params)
     ctxs = [rt.Context(workspace_bytes=reserve) for _ in range(n_streams)]
     held = [c.workspace_bytes() for c in ctxs]
