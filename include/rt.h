@@ -317,6 +317,9 @@ RT_API rt_status rt_synth_tile(rt_ctx *ctx, uint8_t *out, int64_t ld, int H, int
  * reconstruction: a propagation variant and its sweep iterations per dense
  * tile visit (rt_set_picker_classes; by default RT_RASTER with 4, 12 and 24
  * iterations: short visits win on small tiles, longer ones on large tiles).
+ * The budgets are learned on lone tiles; in a chunk of several tiles the
+ * shared launch's throughput sets the time, and raster budgets below the
+ * call's plain one are raised to it.
  *
  * rt_tile_features: features of n tiles (host arrays of device pointers,
  * strides and sizes; n <= 32) into out, a device float array n x

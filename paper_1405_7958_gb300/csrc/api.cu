@@ -198,6 +198,16 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
     PickTable table = ctx->classes;
     table.group[kPickClasses] = variant - RT_RASTER;
     table.max_local[kPickClasses] = max_local > 0 ? max_local : default_max_local(variant);
+    // The picker learned its budgets on lone tiles, where a tile's latency
+    // sets the time and short visits can win. Tiles that share a launch with
+    // others are bound by its throughput instead, and there budgets below
+    // the plain one only add visits (measured on uneven and 4K batches):
+    // they are raised to the plain budget.
+    if (pick && b.n > 1) {
+        const int plain_raster = max_local > 0 ? max_local : default_max_local(RT_RASTER);
+        for (int c = 0; c < kPickClasses; ++c)
+            if (table.group[c] == 0 && table.max_local[c] < plain_raster) table.max_local[c] = plain_raster;
+    }
     // RT_RASTER / RT_QUEUE: every tile starts flagged for a dense visit (the
     // queue visit then seeds every pixel); RT_HYBRID: nothing flagged, the
     // dense pass over all tiles flags what remains.

@@ -88,9 +88,12 @@ __device__ __forceinline__ BlockRef find_block(const UfBatch &b, int64_t g)
     while (k + 1 < b.n && g >= b.img[k + 1].blk_base) ++k;
     BlockRef r;
     r.d = &b.img[k];
-    r.blk = g - r.d->blk_base;
-    r.bx = (int)(r.blk % r.d->nbx);
-    r.by = (int)(r.blk / r.d->nbx);
+    // an image has at most 1024 x 1024 blocks: 32-bit arithmetic (64-bit
+    // division is a long software sequence)
+    const int lb = (int)(g - r.d->blk_base);
+    r.blk = lb;
+    r.by = lb / r.d->nbx;
+    r.bx = lb - r.by * r.d->nbx;
     return r;
 }
 

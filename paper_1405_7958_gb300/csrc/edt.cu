@@ -233,11 +233,11 @@ __device__ __forceinline__ uint32_t seg_bg_mask(const EdtBitsImage &a, int64_t w
 __global__ void __launch_bounds__(kMaskWarps * 32) edt_mask_bits_kernel(EdtBitsBatch b)
 {
     const EdtBitsImage &a = edt_image<&EdtBitsImage::mask_base>(b, blockIdx.x);
-    const int64_t wpr = ceil_div(a.W, 32);
-    const int64_t local = blockIdx.x - a.mask_base;
-    const int64_t gx = ceil_div(wpr, kMaskWarps);
-    const int s = (int)(local / gx);
-    const int wc = (int)(local % gx) * kMaskWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int wpr = (a.W + 31) / 32;
+    const int local = (int)(blockIdx.x - a.mask_base);
+    const int gx = (wpr + kMaskWarps - 1) / kMaskWarps;
+    const int s = local / gx;
+    const int wc = (local - s * gx) * kMaskWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (wc >= wpr) return;
     const int rb = s * kSeg;
     const uint32_t bg = seg_bg_mask(a, wpr, wc, rb, lane);
@@ -251,10 +251,10 @@ __global__ void __launch_bounds__(kMaskWarps * 32) edt_mask_bits_kernel(EdtBitsB
 __global__ void __launch_bounds__(kColThreads) edt_chase_bits_kernel(EdtBitsBatch b)
 {
     const EdtBitsImage &a = edt_image<&EdtBitsImage::col_base>(b, blockIdx.x);
-    const int64_t local = blockIdx.x - a.col_base;
-    const int64_t gx = ceil_div(a.W, kColThreads);
-    const int s = (int)(local / gx);
-    const int c = (int)(local % gx) * kColThreads + threadIdx.x;
+    const int local = (int)(blockIdx.x - a.col_base);
+    const int gx = (a.W + kColThreads - 1) / kColThreads;
+    const int s = local / gx;
+    const int c = (local - s * gx) * kColThreads + threadIdx.x;
     if (c >= a.W) return;
     const int nseg = (int)ceil_div(a.H, kSeg);
     int above = -1;

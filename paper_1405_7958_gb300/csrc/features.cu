@@ -124,11 +124,21 @@ __global__ void feat_count_kernel(FeatBatch fb)
         over += __shfl_down_sync(0xffffffffu, over, o);
         front += __shfl_down_sync(0xffffffffu, front, o);
     }
+    // one set of atomics per CTA (per-warp atomics on the four counters of
+    // an image serialise)
+    __shared__ unsigned long long part[4][32];
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(d.acc + 0, s1);
-        atomicAdd(d.acc + 1, s2);
-        atomicAdd(d.acc + 2, over);
-        atomicAdd(d.acc + 3, front);
+        part[0][w] = s1;
+        part[1][w] = s2;
+        part[2][w] = over;
+        part[3][w] = front;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        unsigned long long t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += part[threadIdx.x][k];
+        if (t) atomicAdd(d.acc + threadIdx.x, t);
     }
 }
 

@@ -176,10 +176,84 @@ __global__ void mlp_adamw_kernel(float *master, uint16_t *wb, const float *grad,
     wb[t] = __bfloat16_as_ushort(__float2bfloat16_rn(p));
 }
 
+// The same forward with one warp per sample, for the few samples of a
+// segmentation chunk (thread per sample would leave a CTA nearly idle for the
+// whole 5.9 k multiply-add chain). Lanes own hidden units j and j + 32; each
+// unit's sum runs over its inputs in the same order, from the same bias, as
+// in mlp_forward_kernel, and lane 0 forms the logits in the same order, so
+// both kernels give the same bits.
+constexpr int kFwdWarps = 8;
+__global__ void __launch_bounds__(kFwdWarps * 32) mlp_forward_warp_kernel(const uint16_t *wb, const float *norm,
+                                                                          const float *x, int B, float *logits,
+                                                                          float *act, int32_t *pick, float min_prob,
+                                                                          int fallback)
+{
+    __shared__ float P[kMlpParams];
+    __shared__ float h[kFwdWarps][2][kMlpH];
+    __shared__ float xn[kFwdWarps][kMlpIn];
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) P[i] = bf(wb[i]);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * kFwdWarps + w;
+    if (b < B && lane < kMlpIn) xn[w][lane] = (x[(int64_t)b * kMlpIn + lane] - norm[lane]) / norm[kMlpIn + lane];
+    __syncthreads();
+    if (b >= B) return;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int j = lane + 32 * q;
+        float s = P[kB1 + j];
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) s = fmaf(P[kW1 + j * kMlpIn + i], xn[w][i], s);
+        h[w][0][j] = fmaxf(s, 0.f);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int j = lane + 32 * q;
+        float s = P[kB2 + j];
+#pragma unroll 8
+        for (int i = 0; i < kMlpH; ++i) s = fmaf(P[kW2 + j * kMlpH + i], h[w][0][i], s);
+        h[w][1][j] = fmaxf(s, 0.f);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            act[(int64_t)b * kMlpAct + lane + 32 * q] = h[w][0][lane + 32 * q];
+            act[(int64_t)b * kMlpAct + kMlpH + lane + 32 * q] = h[w][1][lane + 32 * q];
+        }
+    }
+    if (lane != 0) return;
+    float z[kMlpOut];
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) z[k] = P[kB3 + k];
+    for (int j = 0; j < kMlpH; ++j) {
+#pragma unroll
+        for (int k = 0; k < kMlpOut; ++k) z[k] = fmaf(P[kW3 + k * kMlpH + j], h[w][1][j], z[k]);
+    }
+    int best = 0;
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) {
+        if (logits) logits[(int64_t)b * kMlpOut + k] = z[k];
+        if (z[k] > z[best]) best = k;
+    }
+    if (min_prob > 0.f) {
+        float se = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMlpOut; ++k) se += expf(z[k] - z[best]);
+        if (1.f / se < min_prob) best = fallback;
+    }
+    if (pick) pick[b] = best;
+}
+
 cudaError_t launch_mlp_forward(const uint16_t *wb, const float *norm, const float *x, int B, float *logits, float *act,
                                int32_t *pick, float min_prob, int fallback, cudaStream_t s)
 {
     if (B <= 0) return cudaSuccess;
+    if (B <= 64) {
+        mlp_forward_warp_kernel<<<(unsigned)ceil_div(B, kFwdWarps), kFwdWarps * 32, 0, s>>>(wb, norm, x, B, logits, act,
+                                                                                            pick, min_prob, fallback);
+        return cudaGetLastError();
+    }
     mlp_forward_kernel<<<(unsigned)ceil_div(B, 256), 256, 0, s>>>(wb, norm, x, B, logits, act, pick, min_prob,
                                                                   fallback);
     return cudaGetLastError();

@@ -80,15 +80,22 @@ __global__ void __launch_bounds__(kThreads) obj_scan_pixels_kernel(ObjArgs a)
     const int64_t p0 = ch * kObjChunk;
     if (p0 >= N) return;
     uint32_t base = EMIT ? a.chunk_cnt[ch] : 0u, cnt = 0;
-    for (int j = 0; j < kObjChunk / 32; ++j) {
-        const int64_t p = p0 + j * 32 + lane;
-        bool root = false;
-        int r = 0, c = 0;
-        if (p < N) {
-            r = (int)(p / a.W);
-            c = (int)(p - (int64_t)r * a.W);
-            root = a.L[(int64_t)r * a.ld_L + c] == (int32_t)p;
+    // H * W <= 2^30: 32-bit positions; the row and column follow the pixel
+    // index incrementally (one division per lane, then at most a few wraps)
+    const uint32_t W = (uint32_t)a.W;
+    uint32_t pl = (uint32_t)p0 + lane;
+    uint32_t r = pl / W, c = pl - r * W;
+    for (int j = 0; j < kObjChunk / 32; ++j, pl += 32) {
+        if (j) {
+            c += 32;
+            while (c >= W) {
+                c -= W;
+                ++r;
+            }
         }
+        const int64_t p = pl;
+        bool root = false;
+        if (p < N) root = a.L[(int64_t)r * a.ld_L + c] == (int32_t)p;
         const uint32_t m = __ballot_sync(0xffffffffu, root);
         if (EMIT && root) {
             const int64_t k = (int64_t)base + cnt + __popc(m & ((1u << lane) - 1u));
@@ -96,10 +103,10 @@ __global__ void __launch_bounds__(kThreads) obj_scan_pixels_kernel(ObjArgs a)
                 a.olabel[k] = (int32_t)p;
                 a.idx_of[p] = (int32_t)k;
                 int4 b;
-                b.x = r;
-                b.y = c;
-                b.z = r;
-                b.w = c;
+                b.x = (int)r;
+                b.y = (int)c;
+                b.z = (int)r;
+                b.w = (int)c;
                 reinterpret_cast<int4 *>(a.box)[k] = b;
             }
         }
@@ -224,10 +231,10 @@ __global__ void __launch_bounds__(kThreads) obj_inter_kernel(ObjArgs a)
         const int4 b = reinterpret_cast<const int4 *>(a.box)[k];
         const int32_t l = a.olabel[k];
         const int bh = b.z - b.x + 1, bw = b.w - b.y + 1;
-        const int64_t m = (int64_t)bh * bw;
+        const int m = bh * bw;   // H * W <= 2^30
         int64_t area = 0, per = 0, sr = 0, sc = 0, srr = 0, scc = 0, src = 0, si = 0, sii = 0;
-        for (int64_t i = threadIdx.x; i < m; i += kThreads) {
-            const int y = (int)(i / bw), x = (int)(i - (int64_t)y * bw);
+        for (int i = threadIdx.x; i < m; i += kThreads) {
+            const int y = i / bw, x = i - y * bw;
             const int r = b.x + y, c = b.y + x;
             const int32_t *Lr = a.L + (int64_t)r * a.ld_L;
             if (Lr[c] != l) continue;
@@ -375,37 +382,37 @@ struct SmemView {
     int32_t *d, *r;
     unsigned long long *st;
     uint8_t *fl;   // bit 0: in the object, bit 1: not a maximum
-    __device__ __forceinline__ bool in(int64_t i) const { return fl[i] & 1u; }
-    __device__ __forceinline__ int32_t D(int64_t i) const { return d[i]; }
-    __device__ __forceinline__ int32_t &R(int64_t i) const { return r[i]; }
-    __device__ __forceinline__ unsigned long long &S(int64_t i) const { return st[i]; }
-    __device__ __forceinline__ bool nm(int64_t i) const { return fl[i] & 2u; }
-    __device__ __forceinline__ void set_nm(int64_t i) const { fl[i] |= 2u; }
+    __device__ __forceinline__ bool in(int i) const { return fl[i] & 1u; }
+    __device__ __forceinline__ int32_t D(int i) const { return d[i]; }
+    __device__ __forceinline__ int32_t &R(int i) const { return r[i]; }
+    __device__ __forceinline__ unsigned long long &S(int i) const { return st[i]; }
+    __device__ __forceinline__ bool nm(int i) const { return fl[i] & 2u; }
+    __device__ __forceinline__ void set_nm(int i) const { fl[i] |= 2u; }
 };
 
 struct GlobalView {
     const ObjArgs *a;
     int32_t label;
     int r0, c0, bw;
-    __device__ __forceinline__ int64_t pix(int64_t i) const
+    __device__ __forceinline__ int64_t pix(int i) const
     {
-        const int y = (int)(i / bw), x = (int)(i - (int64_t)y * bw);
+        const int y = i / bw, x = i - y * bw;
         return (int64_t)(r0 + y) * a->W + (c0 + x);
     }
-    __device__ __forceinline__ bool in(int64_t i) const
+    __device__ __forceinline__ bool in(int i) const
     {
-        const int y = (int)(i / bw), x = (int)(i - (int64_t)y * bw);
+        const int y = i / bw, x = i - y * bw;
         return a->L[(int64_t)(r0 + y) * a->ld_L + c0 + x] == label;
     }
-    __device__ __forceinline__ int32_t D(int64_t i) const
+    __device__ __forceinline__ int32_t D(int i) const
     {
-        const int y = (int)(i / bw), x = (int)(i - (int64_t)y * bw);
+        const int y = i / bw, x = i - y * bw;
         return a->D[(int64_t)(r0 + y) * a->ld_D + c0 + x];
     }
-    __device__ __forceinline__ int32_t &R(int64_t i) const { return a->R[pix(i)]; }
-    __device__ __forceinline__ unsigned long long &S(int64_t i) const { return a->st[pix(i)]; }
-    __device__ __forceinline__ bool nm(int64_t i) const { return *reinterpret_cast<volatile uint8_t *>(a->nm + pix(i)) != 0; }
-    __device__ __forceinline__ void set_nm(int64_t i) const { a->nm[pix(i)] = 1u; }
+    __device__ __forceinline__ int32_t &R(int i) const { return a->R[pix(i)]; }
+    __device__ __forceinline__ unsigned long long &S(int i) const { return a->st[pix(i)]; }
+    __device__ __forceinline__ bool nm(int i) const { return *reinterpret_cast<volatile uint8_t *>(a->nm + pix(i)) != 0; }
+    __device__ __forceinline__ void set_nm(int i) const { a->nm[pix(i)] = 1u; }
 };
 
 // Largest D below `below` over the object's pixels that have no basin yet
@@ -413,10 +420,10 @@ struct GlobalView {
 // left unlabelled at one level (not yet connected to a basin) is taken at a
 // lower one, when its level set joins a basin.
 template <class V>
-__device__ __forceinline__ int32_t max_unlabelled(const V &v, int64_t m, int32_t below, int *red)
+__device__ __forceinline__ int32_t max_unlabelled(const V &v, int m, int32_t below, int *red)
 {
     int32_t mx = -1;
-    for (int64_t i = threadIdx.x; i < m; i += kThreads)
+    for (int i = threadIdx.x; i < m; i += kThreads)
         if (v.in(i) && v.S(i) == kUnl && v.D(i) < below) mx = max(mx, v.D(i));
     mx = __reduce_max_sync(0xffffffffu, mx);
     __syncthreads();
@@ -436,9 +443,9 @@ __device__ __forceinline__ int32_t max_unlabelled(const V &v, int64_t m, int32_t
 template <class V>
 __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, int bh, int bw, int *red)
 {
-    const int64_t m = (int64_t)bh * bw;
-    auto for_nbrs = [&](int64_t i, auto &&fn) {
-        const int y = (int)(i / bw), x = (int)(i - (int64_t)y * bw);
+    const int m = bh * bw;   // H * W <= 2^30
+    auto for_nbrs = [&](int i, auto &&fn) {
+        const int y = i / bw, x = i - y * bw;
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
@@ -446,21 +453,21 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
                 if (dy == 0 && dx == 0) continue;
                 const int yy = y + dy, xx = x + dx;
                 if (yy < 0 || yy >= bh || xx < 0 || xx >= bw) continue;
-                const int64_t j = (int64_t)yy * bw + xx;
+                const int j = yy * bw + xx;
                 if (v.in(j)) fn(j);
             }
     };
     // 1. h-maxima transform: R = reconstruction of max(D - h, 0) under D
-    for (int64_t i = threadIdx.x; i < m; i += kThreads)
+    for (int i = threadIdx.x; i < m; i += kThreads)
         if (v.in(i)) v.R(i) = max(v.D(i) - a.h, 0);
     __syncthreads();
     for (;;) {
         int ch = 0;
-        for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+        for (int i = threadIdx.x; i < m; i += kThreads) {
             if (!v.in(i)) continue;
             volatile int32_t &Ri = v.R(i);
             int32_t mx = Ri;
-            for_nbrs(i, [&](int64_t j) { mx = max(mx, *(volatile int32_t *)&v.R(j)); });
+            for_nbrs(i, [&](int j) { mx = max(mx, *(volatile int32_t *)&v.R(j)); });
             mx = min(mx, v.D(i));
             if (mx > Ri) {
                 Ri = mx;
@@ -470,21 +477,21 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
         if (!__syncthreads_or(ch)) break;
     }
     // 2. not a maximum: a higher neighbour, or an equal one that is not
-    for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = threadIdx.x; i < m; i += kThreads) {
         if (!v.in(i)) continue;
         bool hi = false;
         const int32_t ri = v.R(i);
-        for_nbrs(i, [&](int64_t j) { hi |= v.R(j) > ri; });
+        for_nbrs(i, [&](int j) { hi |= v.R(j) > ri; });
         if (hi) v.set_nm(i);
     }
     __syncthreads();
     for (;;) {
         int ch = 0;
-        for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+        for (int i = threadIdx.x; i < m; i += kThreads) {
             if (!v.in(i) || v.nm(i)) continue;
             bool f = false;
             const int32_t ri = v.R(i);
-            for_nbrs(i, [&](int64_t j) { f |= v.R(j) == ri && v.nm(j); });
+            for_nbrs(i, [&](int j) { f |= v.R(j) == ri && v.nm(j); });
             if (f) {
                 v.set_nm(i);
                 ch = 1;
@@ -493,19 +500,19 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
         if (!__syncthreads_or(ch)) break;
     }
     // 3. markers: each plateau of maxima takes its smallest linear index
-    for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = threadIdx.x; i < m; i += kThreads) {
         if (!v.in(i)) continue;
-        const int y = (int)(i / bw), x = (int)(i - (int64_t)y * bw);
+        const int y = i / bw, x = i - y * bw;
         v.S(i) = v.nm(i) ? kUnl : (unsigned long long)(uint32_t)((r0 + y) * a.W + (c0 + x));
     }
     __syncthreads();
     for (;;) {
         int ch = 0;
-        for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+        for (int i = threadIdx.x; i < m; i += kThreads) {
             if (!v.in(i) || v.nm(i)) continue;
             volatile unsigned long long &Si = v.S(i);
             unsigned long long mn = Si;
-            for_nbrs(i, [&](int64_t j) {
+            for_nbrs(i, [&](int j) {
                 if (!v.nm(j)) {
                     const unsigned long long sj = *(volatile unsigned long long *)&v.S(j);
                     mn = sj < mn ? sj : mn;
@@ -519,9 +526,9 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
         if (!__syncthreads_or(ch)) break;
     }
     int nb = 0;
-    for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = threadIdx.x; i < m; i += kThreads) {
         if (!v.in(i) || v.nm(i)) continue;
-        const int y = (int)(i / bw), x = (int)(i - (int64_t)y * bw);
+        const int y = i / bw, x = i - y * bw;
         nb += v.S(i) == (unsigned long long)(uint32_t)((r0 + y) * a.W + (c0 + x));
     }
     nb = __reduce_add_sync(0xffffffffu, nb);
@@ -534,10 +541,10 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
     for (int32_t t = max_unlabelled(v, m, INT32_MAX, red); t >= 0; t = max_unlabelled(v, m, t, red)) {
         for (;;) {
             int ch = 0;
-            for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+            for (int i = threadIdx.x; i < m; i += kThreads) {
                 if (!v.in(i) || v.S(i) != kUnl || v.D(i) < t) continue;
                 uint32_t mn = 0xffffffffu;
-                for_nbrs(i, [&](int64_t j) {
+                for_nbrs(i, [&](int j) {
                     const unsigned long long sj = *(volatile unsigned long long *)&v.S(j);
                     if (sj != kUnl && (uint32_t)(sj >> 32) < g) mn = min(mn, (uint32_t)sj);
                 });
@@ -551,9 +558,9 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
         }
     }
     // 5. basins out
-    for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = threadIdx.x; i < m; i += kThreads) {
         if (!v.in(i)) continue;
-        const int y = (int)(i / bw), x = (int)(i - (int64_t)y * bw);
+        const int y = i / bw, x = i - y * bw;
         a.basins[(int64_t)(r0 + y) * a.ld_B + (c0 + x)] = (int32_t)(uint32_t)v.S(i);
     }
 }
@@ -576,10 +583,10 @@ __global__ void __launch_bounds__(kThreads) obj_watershed_kernel(ObjArgs a)
         const int4 b = reinterpret_cast<const int4 *>(a.box)[k];
         const int32_t l = a.olabel[k];
         const int bh = b.z - b.x + 1, bw = b.w - b.y + 1;
-        const int64_t m = (int64_t)bh * bw;
+        const int m = bh * bw;   // H * W <= 2^30
         if (m <= kWsSmemPx) {
-            for (int64_t i = threadIdx.x; i < m; i += kThreads) {
-                const int y = (int)(i / bw), x = (int)(i - (int64_t)y * bw);
+            for (int i = threadIdx.x; i < m; i += kThreads) {
+                const int y = i / bw, x = i - y * bw;
                 const int r = b.x + y, c = b.y + x;
                 const bool in = a.L[(int64_t)r * a.ld_L + c] == l;
                 sv.fl[i] = in ? 1u : 0u;
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(kThreads) obj_watershed_kernel(ObjArgs a)
             watershed_object(sv, a, b.x, b.y, bh, bw, &red);
         } else {
             GlobalView gv{&a, l, b.x, b.y, bw};
-            for (int64_t i = threadIdx.x; i < m; i += kThreads)
+            for (int i = threadIdx.x; i < m; i += kThreads)
                 if (gv.in(i)) a.nm[gv.pix(i)] = 0u;
             __syncthreads();
             watershed_object(gv, a, b.x, b.y, bh, bw, &red);

@@ -89,6 +89,20 @@ def test_mlp_forward_and_backward_match_oracle(rt):
     assert np.isclose(float(host(loss)[0]), OM.loss(p, norm, x, y), rtol=1e-5)
 
 
+def test_mlp_forward_small_and_large_batches_agree(rt):
+    """Chunks of up to 64 samples run one warp per sample, larger batches one
+    thread per sample: the same sums in the same order, the same bits."""
+    rng = np.random.default_rng(2)
+    pk = rt.Picker(seed=3)
+    x, _ = _picker_inputs(rng, 300)
+    xd = torch.from_numpy(x).cuda()
+    big_logits, big_act, big_pick = pk.forward(xd, with_act=True, min_prob=0.5)
+    for n in (1, 7, 64):
+        logits, act, pick = pk.forward(xd[:n].contiguous(), with_act=True, min_prob=0.5)
+        assert torch.equal(logits, big_logits[:n]) and torch.equal(act, big_act[:n])
+        assert torch.equal(pick, big_pick[:n])
+
+
 def test_adamw_step_matches_oracle(rt):
     rng = np.random.default_rng(2)
     pk = rt.Picker(seed=3)
@@ -255,11 +269,13 @@ def test_trained_picker_report_replays_on_the_gpu(rt):
 
 def test_trained_picker_on_new_held_out_tiles(rt):
     """16 new held-out uneven tiles (seeds outside the training and
-    evaluation sets) run batched with the trained picker (confidence
-    fall-back at 0.6) and with the plain schedule: identical outputs; the
-    picks spread over the classes; the measured time (median of 5, CUDA
-    events) is printed, and the picker's own cost (features and network) is
-    bounded."""
+    evaluation sets), each alone (the regime the picker was trained in) and
+    all in one call, with the trained picker (confidence fall-back at 0.6)
+    and with the plain schedule: identical outputs; the measured times
+    (median of 5, CUDA events) are printed. The gain over the plain schedule
+    net of the picker's own cost (features and network) is bounded below; the
+    picker's gain before its cost is asserted on the committed held-out set
+    (test_trained_picker_report_replays_on_the_gpu)."""
     import statistics
     _, pk, _, _, _ = _trained(rt)
     specs = synth.batch_sizes(16, 9100)
@@ -267,29 +283,35 @@ def test_trained_picker_on_new_held_out_tiles(rt):
     ctx_l, ctx_p = rt.Context(), rt.Context()
     pk.attach(ctx_l)
     learned, plain = rt.SegParams(policy=1, pick_min_prob=600), rt.SegParams()
-    ol = rt.segment_batch(imgs, learned, ctx=ctx_l)
-    op = rt.segment_batch(imgs, plain, ctx=ctx_p)
-    torch.cuda.synchronize()
-    for a, b in zip(ol, op):
-        for k in ("R", "F", "L", "D"):
-            assert torch.equal(a[k], b[k])
-    picks = rt.last_picks(ctx_l)
-    assert len(picks) == 16 and all(0 <= c <= 3 for c in picks)
 
-    def timed(params, ctx, outs):
+    def timed(batch, params, ctx, outs):
         ts = []
         for _ in range(5):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            rt.segment_batch(imgs, params, outputs=outs, ctx=ctx)
+            rt.segment_batch(batch, params, outputs=outs, ctx=ctx)
             e1.record()
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    t_learned, t_plain = timed(learned, ctx_l, ol), timed(plain, ctx_p, op)
-    gain = t_plain / t_learned
-    print(f"trained picker: {t_learned:.2f} ms, plain: {t_plain:.2f} ms, gain {gain:.3f}, picks {picks}")
-    assert gain > 0.95
+    gains = {}
+    for mode, groups in (("alone", [[im] for im in imgs]), ("batched", [imgs])):
+        t_l = t_p = 0.0
+        picks = []
+        for g in groups:
+            ol = rt.segment_batch(g, learned, ctx=ctx_l)
+            picks += rt.last_picks(ctx_l)
+            op = rt.segment_batch(g, plain, ctx=ctx_p)
+            torch.cuda.synchronize()
+            for a, b in zip(ol, op):
+                for k in ("R", "F", "L", "D"):
+                    assert torch.equal(a[k], b[k])
+            t_l += timed(g, learned, ctx_l, ol)
+            t_p += timed(g, plain, ctx_p, op)
+        assert len(picks) == 16 and all(0 <= c <= 3 for c in picks)
+        gains[mode] = t_p / t_l
+        print(f"{mode}: trained picker {t_l:.2f} ms, plain {t_p:.2f} ms, gain {gains[mode]:.3f}, picks {picks}")
+    assert min(gains.values()) > 0.95
     ctx_l.close()
     ctx_p.close()
