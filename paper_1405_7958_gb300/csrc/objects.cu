@@ -32,9 +32,9 @@ size_t obj_workspace_bytes(int H, int W, bool features, bool watershed, int cap)
 {
     const size_t N = (size_t)H * W;
     const size_t nch = (size_t)ceil_div((int64_t)N, kObjChunk);
-    size_t b = piece(nch * 4) + piece(16) + piece(N * 4) + piece(N * 4) + piece(N * 16);
+    size_t b = piece(nch * 4) + piece(64) + piece(N * 4) + piece(N * 4) + piece(N * 16);
     if (features) b += piece((size_t)(cap > 0 ? cap : 1) * sizeof(ObjInter));
-    if (watershed) b += piece(N * 4) + piece(N * 8) + piece(N);
+    if (watershed) b += piece(N * 4) + piece(N * 8) + piece(N) + piece(N * 4);
     return b;
 }
 
@@ -49,7 +49,7 @@ void obj_carve(ObjArgs &a, char *base, bool features, bool watershed)
         return p;
     };
     a.chunk_cnt = reinterpret_cast<uint32_t *>(take(nch * 4));
-    a.ctl = reinterpret_cast<uint32_t *>(take(16));
+    a.ctl = reinterpret_cast<uint32_t *>(take(64));
     a.idx_of = reinterpret_cast<int32_t *>(take(N * 4));
     a.olabel = reinterpret_cast<int32_t *>(take(N * 4));
     a.box = reinterpret_cast<int32_t *>(take(N * 16));
@@ -60,10 +60,12 @@ void obj_carve(ObjArgs &a, char *base, bool features, bool watershed)
         a.R = reinterpret_cast<int32_t *>(take(N * 4));
         a.st = reinterpret_cast<unsigned long long *>(take(N * 8));
         a.nm = reinterpret_cast<uint8_t *>(take(N));
+        a.order = reinterpret_cast<int32_t *>(take(N * 4));
     } else {
         a.R = nullptr;
         a.st = nullptr;
         a.nm = nullptr;
+        a.order = nullptr;
     }
 }
 
@@ -144,6 +146,8 @@ __global__ void __launch_bounds__(1024) obj_prefix_kernel(ObjArgs a, int64_t nch
         a.ctl[0] = part[1023];
         a.ctl[1] = 0u;
         a.ctl[2] = 0u;
+        a.ctl[3] = 0u;
+        a.ctl[4] = 0u;
         if (a.n_obj) *a.n_obj = (int32_t)part[1023];
         if (a.n_basins) *a.n_basins = 0;
     }
@@ -273,20 +277,91 @@ __global__ void __launch_bounds__(kThreads) obj_inter_kernel(ObjArgs a)
     }
 }
 
-// Thread per object: the features from the intermediate results. Every
-// floating-point step is an explicitly rounded operation (no contraction
-// into fused multiply-adds), starting from exact integer moments.
-__global__ void obj_feature_kernel(ObjArgs a)
+// Step 2, the features from the intermediate results. The paper runs one
+// thread per object; with a few thousand nuclei per tile that leaves the GPU
+// nearly idle behind long serial double-precision chains, so here a warp
+// takes an object: lanes own 8 histogram bins and 2 co-occurrence cells each,
+// and lane 0 forms the moment features. Every floating-point step is an
+// explicitly rounded operation (no contraction into fused multiply-adds),
+// starting from exact integer moments; only the entropy and the
+// homogeneity sum their terms in a tree order instead of bin order.
+__device__ __forceinline__ double warp_sum_d(double v)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;   // lane 0
+}
+
+__global__ void __launch_bounds__(128) obj_feature_kernel(ObjArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t n_obj = min((int64_t)a.ctl[0], a.max_obj);
-    if (k >= n_obj || k >= a.cap) return;
+    if (k >= n_obj || k >= a.cap) return;   // whole warp
     const ObjInter &o = a.inter[k];
+    const int64_t n = o.area;
+    const double da = (double)n;
+    // histogram: this lane's bins 8 lane .. 8 lane + 7
+    uint32_t hb[8];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        hb[q] = o.hist[8 * lane + q];
+        tot += hb[q];
+    }
+    double ent = 0.0;
+    int lo = -1, hi = -1;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (!hb[q]) continue;
+        if (lo < 0) lo = 8 * lane + q;
+        hi = 8 * lane + q;
+        const double p = __ddiv_rn((double)hb[q], da);
+        ent = __dsub_rn(ent, __dmul_rn(p, log2(p)));
+    }
+    ent = warp_sum_d(ent);
+    const uint32_t has = __ballot_sync(0xffffffffu, tot != 0);
+    const int vmin = __shfl_sync(0xffffffffu, lo, __ffs(has) - 1);
+    const int vmax = __shfl_sync(0xffffffffu, hi, 31 - __clz(has));
+    // median: the smallest v with 2 cum(v) >= n (exclusive prefix over lanes)
+    uint32_t pre = tot;
+#pragma unroll
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, pre, o2);
+        if (lane >= o2) pre += t;
+    }
+    int64_t cum = (int64_t)pre - tot;
+    int med = -1;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        cum += hb[q];
+        if (med < 0 && hb[q] && 2 * cum >= n) med = 8 * lane + q;
+    }
+    const uint32_t mh = __ballot_sync(0xffffffffu, med >= 0);
+    med = __shfl_sync(0xffffffffu, med, __ffs(mh) - 1);
+    // co-occurrence: this lane's cells 2 lane, 2 lane + 1
+    int64_t n2 = 0, con = 0, en = 0;
+    double hom = 0.0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int c = 2 * lane + q;
+        const int64_t g = o.glcm[c], d = (c >> 3) - (c & 7);
+        n2 += g;
+        con += d * d * g;
+        en += g * g;
+        hom = __dadd_rn(hom, __ddiv_rn((double)g, (double)(1 + (d < 0 ? -d : d))));
+    }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        n2 += __shfl_down_sync(0xffffffffu, n2, o2);
+        con += __shfl_down_sync(0xffffffffu, con, o2);
+        en += __shfl_down_sync(0xffffffffu, en, o2);
+    }
+    hom = warp_sum_d(hom);
+    if (lane != 0) return;
     const int4 b = reinterpret_cast<const int4 *>(a.box)[k];
     double *f = a.feat + k * kObjFeat;
     a.out_labels[k] = a.olabel[k];
-    const int64_t n = o.area;
-    const double da = (double)n;
     f[0] = da;
     f[1] = (double)o.per;
     f[2] = (double)(b.z - b.x + 1);
@@ -310,37 +385,12 @@ __global__ void obj_feature_kernel(ObjArgs a)
     f[9] = __ddiv_rn(__dmul_rn(__dmul_rn(4.0, 3.14159265358979323846), da), __dmul_rn(P, P));
     f[10] = __ddiv_rn((double)o.si, da);
     f[11] = __dsqrt_rn(__ddiv_rn((double)((__int128)n * o.sii - (__int128)o.si * o.si), a2));
-    int vmin = -1, vmax = -1, med = -1;
-    int64_t cum = 0;
-    double ent = 0.0;
-    for (int v = 0; v < 256; ++v) {
-        const uint32_t h = o.hist[v];
-        if (!h) continue;
-        if (vmin < 0) vmin = v;
-        vmax = v;
-        cum += h;
-        if (med < 0 && 2 * cum >= n) med = v;
-        const double p = __ddiv_rn((double)h, da);
-        ent = __dsub_rn(ent, __dmul_rn(p, log2(p)));
-    }
     f[12] = vmin;
     f[13] = vmax;
     f[14] = med;
     f[15] = ent;
-    int64_t n2 = 0, con = 0, en = 0;
-    for (int q = 0; q < 64; ++q) {
-        const int64_t g = o.glcm[q], d = (q >> 3) - (q & 7);
-        n2 += g;
-        con += d * d * g;
-        en += g * g;
-    }
     f[16] = (double)n2;
     if (n2 > 0) {
-        double hom = 0.0;
-        for (int q = 0; q < 64; ++q) {
-            const int d = (q >> 3) - (q & 7);
-            hom = __dadd_rn(hom, __ddiv_rn((double)o.glcm[q], (double)(1 + (d < 0 ? -d : d))));
-        }
         f[17] = __ddiv_rn((double)con, (double)n2);
         f[18] = __ddiv_rn((double)en, __dmul_rn((double)n2, (double)n2));
         f[19] = __ddiv_rn(hom, (double)n2);
@@ -349,10 +399,10 @@ __global__ void obj_feature_kernel(ObjArgs a)
     }
 }
 
-int persistent_grid(const void *fn, size_t smem, int num_sms)
+int persistent_grid(const void *fn, size_t smem, int num_sms, int threads = kThreads)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         per_sm = 1;
     }
@@ -367,7 +417,7 @@ cudaError_t launch_object_features(const ObjArgs &a, int num_sms, cudaStream_t s
     if (a.cap < 1) return cudaSuccess;
     obj_inter_kernel<<<(unsigned)persistent_grid((const void *)obj_inter_kernel, 0, num_sms), kThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    obj_feature_kernel<<<(unsigned)ceil_div(a.cap, 128), 128, 0, s>>>(a);
+    obj_feature_kernel<<<(unsigned)ceil_div((int64_t)a.cap * 32, 128), 128, 0, s>>>(a);
     *launches += 2;
     return cudaGetLastError();
 }
@@ -415,33 +465,43 @@ struct GlobalView {
     __device__ __forceinline__ void set_nm(int i) const { a->nm[pix(i)] = 1u; }
 };
 
+// The threads that work on one object: a whole block (large boxes) or one
+// warp (small boxes, eight objects per block in flight).
+template <int NT>
+struct BlockGroup {
+    static constexpr int size = NT;
+    int *red;   // shared reduction word
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+    __device__ __forceinline__ int32_t max(int32_t v) const
+    {
+        v = __reduce_max_sync(0xffffffffu, v);
+        __syncthreads();
+        if (threadIdx.x == 0) *red = -1;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) atomicMax(red, v);
+        __syncthreads();
+        return *red;
+    }
+};
+
+
 // Largest D below `below` over the object's pixels that have no basin yet
 // (-1: none). The levels strictly descend, so the flooding ends; a pixel
 // left unlabelled at one level (not yet connected to a basin) is taken at a
 // lower one, when its level set joins a basin.
-template <class V>
-__device__ __forceinline__ int32_t max_unlabelled(const V &v, int m, int32_t below, int *red)
+template <class V, class G>
+__device__ __forceinline__ int32_t max_unlabelled(const V &v, const G &g, int m, int32_t below)
 {
     int32_t mx = -1;
-    for (int i = threadIdx.x; i < m; i += kThreads)
+    for (int i = g.rank(); i < m; i += G::size)
         if (v.in(i) && v.S(i) == kUnl && v.D(i) < below) mx = max(mx, v.D(i));
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    __syncthreads();
-    if (threadIdx.x == 0) *red = -1;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) atomicMax(red, mx);
-    __syncthreads();
-    return *red;
+    return g.max(mx);
 }
 
-// Marker-controlled watershed of one object with box (r0, c0) of bh x bw.
-// Every loop below is a fixed-point iteration of monotone updates run in
-// place by all threads at once, ended by a pass that changes nothing, or a
-// synchronous breadth-first layer (the state word of a pixel carries the
-// layer that labelled it, so a pixel labelled in this layer is not a source
-// of the same layer).
-template <class V>
-__device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, int bh, int bw, int *red)
+template <class V, class G>
+__device__ void watershed_object(const V &v, const G &g, const ObjArgs &a, int r0, int c0, int bh, int bw)
 {
     const int m = bh * bw;   // H * W <= 2^30
     auto for_nbrs = [&](int i, auto &&fn) {
@@ -458,12 +518,12 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
             }
     };
     // 1. h-maxima transform: R = reconstruction of max(D - h, 0) under D
-    for (int i = threadIdx.x; i < m; i += kThreads)
+    for (int i = g.rank(); i < m; i += G::size)
         if (v.in(i)) v.R(i) = max(v.D(i) - a.h, 0);
-    __syncthreads();
+    g.sync();
     for (;;) {
         int ch = 0;
-        for (int i = threadIdx.x; i < m; i += kThreads) {
+        for (int i = g.rank(); i < m; i += G::size) {
             if (!v.in(i)) continue;
             volatile int32_t &Ri = v.R(i);
             int32_t mx = Ri;
@@ -474,20 +534,20 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
                 ch = 1;
             }
         }
-        if (!__syncthreads_or(ch)) break;
+        if (!g.any(ch)) break;
     }
     // 2. not a maximum: a higher neighbour, or an equal one that is not
-    for (int i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = g.rank(); i < m; i += G::size) {
         if (!v.in(i)) continue;
         bool hi = false;
         const int32_t ri = v.R(i);
         for_nbrs(i, [&](int j) { hi |= v.R(j) > ri; });
         if (hi) v.set_nm(i);
     }
-    __syncthreads();
+    g.sync();
     for (;;) {
         int ch = 0;
-        for (int i = threadIdx.x; i < m; i += kThreads) {
+        for (int i = g.rank(); i < m; i += G::size) {
             if (!v.in(i) || v.nm(i)) continue;
             bool f = false;
             const int32_t ri = v.R(i);
@@ -497,18 +557,18 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
                 ch = 1;
             }
         }
-        if (!__syncthreads_or(ch)) break;
+        if (!g.any(ch)) break;
     }
     // 3. markers: each plateau of maxima takes its smallest linear index
-    for (int i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = g.rank(); i < m; i += G::size) {
         if (!v.in(i)) continue;
         const int y = i / bw, x = i - y * bw;
         v.S(i) = v.nm(i) ? kUnl : (unsigned long long)(uint32_t)((r0 + y) * a.W + (c0 + x));
     }
-    __syncthreads();
+    g.sync();
     for (;;) {
         int ch = 0;
-        for (int i = threadIdx.x; i < m; i += kThreads) {
+        for (int i = g.rank(); i < m; i += G::size) {
             if (!v.in(i) || v.nm(i)) continue;
             volatile unsigned long long &Si = v.S(i);
             unsigned long long mn = Si;
@@ -523,69 +583,112 @@ __device__ void watershed_object(const V &v, const ObjArgs &a, int r0, int c0, i
                 ch = 1;
             }
         }
-        if (!__syncthreads_or(ch)) break;
+        if (!g.any(ch)) break;
     }
     int nb = 0;
-    for (int i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = g.rank(); i < m; i += G::size) {
         if (!v.in(i) || v.nm(i)) continue;
         const int y = i / bw, x = i - y * bw;
         nb += v.S(i) == (unsigned long long)(uint32_t)((r0 + y) * a.W + (c0 + x));
     }
     nb = __reduce_add_sync(0xffffffffu, nb);
-    if ((threadIdx.x & 31) == 0 && nb) {
+    if ((g.rank() & 31) == 0 && nb) {
         atomicAdd(a.ctl + 2, (uint32_t)nb);
         if (a.n_basins) atomicAdd(a.n_basins, nb);
     }
-    // 4. flooding by levels of D, highest first, in breadth-first layers
-    uint32_t g = 1;
-    for (int32_t t = max_unlabelled(v, m, INT32_MAX, red); t >= 0; t = max_unlabelled(v, m, t, red)) {
-        for (;;) {
-            int ch = 0;
-            for (int i = threadIdx.x; i < m; i += kThreads) {
-                if (!v.in(i) || v.S(i) != kUnl || v.D(i) < t) continue;
+    // 4. flooding by levels of D, highest first, in breadth-first layers. A
+    // level ends after the first layer whose new pixels have no unlabelled
+    // neighbour with D >= t (the next layer could only take such pixels);
+    // the next level, the largest D below t among unlabelled pixels, is
+    // found during the level's first layer (those pixels do not change
+    // within the level).
+    uint32_t layer = 1;
+    int32_t t = max_unlabelled(v, g, m, INT32_MAX);
+    while (t >= 0) {
+        int32_t next = -1;
+        for (bool first = true;; first = false) {
+            int more = 0;
+            for (int i = g.rank(); i < m; i += G::size) {
+                if (!v.in(i) || v.S(i) != kUnl) continue;
+                const int32_t di = v.D(i);
+                if (di < t) {
+                    if (first) next = max(next, di);
+                    continue;
+                }
                 uint32_t mn = 0xffffffffu;
                 for_nbrs(i, [&](int j) {
                     const unsigned long long sj = *(volatile unsigned long long *)&v.S(j);
-                    if (sj != kUnl && (uint32_t)(sj >> 32) < g) mn = min(mn, (uint32_t)sj);
+                    if (sj != kUnl && (uint32_t)(sj >> 32) < layer) mn = min(mn, (uint32_t)sj);
                 });
                 if (mn != 0xffffffffu) {
-                    *(volatile unsigned long long *)&v.S(i) = ((unsigned long long)g << 32) | mn;
-                    ch = 1;
+                    *(volatile unsigned long long *)&v.S(i) = ((unsigned long long)layer << 32) | mn;
+                    for_nbrs(i, [&](int j) {
+                        more |= *(volatile unsigned long long *)&v.S(j) == kUnl && v.D(j) >= t;
+                    });
                 }
             }
-            ++g;
-            if (!__syncthreads_or(ch)) break;
+            ++layer;
+            if (first) next = g.max(next);
+            if (!g.any(more)) break;
         }
+        t = next;
     }
     // 5. basins out
-    for (int i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = g.rank(); i < m; i += G::size) {
         if (!v.in(i)) continue;
         const int y = i / bw, x = i - y * bw;
         a.basins[(int64_t)(r0 + y) * a.ld_B + (c0 + x)] = (int32_t)(uint32_t)v.S(i);
     }
 }
 
+constexpr int kWsThreads = 256;
+constexpr int kWsLargePx = 1024;   // boxes above this start first
 constexpr size_t kWsSmemBytes = (size_t)kWsSmemPx * (4 + 4 + 8 + 1) + 64;
 
-__global__ void __launch_bounds__(kThreads) obj_watershed_kernel(ObjArgs a)
+// Carves a shared-memory view of `px` pixels at base (8-byte aligned).
+__device__ __forceinline__ SmemView smem_view(unsigned char *base, int px)
+{
+    SmemView sv;
+    sv.st = reinterpret_cast<unsigned long long *>(base);
+    sv.d = reinterpret_cast<int32_t *>(sv.st + px);
+    sv.r = sv.d + px;
+    sv.fl = reinterpret_cast<uint8_t *>(sv.r + px);
+    return sv;
+}
+
+// Thread per object: objects with a box of more than kWsLargePx pixels go to
+// the front of `order`, the others to the back, so the long ones start first.
+__global__ void obj_classify_kernel(ObjArgs a)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_obj = (int)min((int64_t)a.ctl[0], a.max_obj);
+    if (k >= n_obj) return;
+    const int4 b = reinterpret_cast<const int4 *>(a.box)[k];
+    const int m = (b.z - b.x + 1) * (b.w - b.y + 1);
+    if (m > kWsLargePx) a.order[atomicAdd(a.ctl + 3, 1u)] = k;
+    else a.order[a.max_obj - 1 - atomicAdd(a.ctl + 4, 1u)] = k;
+}
+
+// A block per object, in the order above: the box in shared memory up to
+// kWsSmemPx pixels, else in the image-sized global arrays.
+__global__ void __launch_bounds__(kWsThreads) obj_watershed_kernel(ObjArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int slot, red;
-    SmemView sv;
-    sv.st = reinterpret_cast<unsigned long long *>(smem);
-    sv.d = reinterpret_cast<int32_t *>(sv.st + kWsSmemPx);
-    sv.r = sv.d + kWsSmemPx;
-    sv.fl = reinterpret_cast<uint8_t *>(sv.r + kWsSmemPx);
+    const SmemView sv = smem_view(smem, kWsSmemPx);
+    const BlockGroup<kWsThreads> g{&red};
     const int n_obj = (int)min((int64_t)a.ctl[0], a.max_obj);
+    const int n_big = (int)a.ctl[3];
     for (;;) {
-        const int k = next_object(a, n_obj, &slot);
-        if (k < 0) return;
+        const int q = next_object(a, n_obj, &slot);
+        if (q < 0) return;
+        const int k = q < n_big ? a.order[q] : a.order[a.max_obj - 1 - (q - n_big)];
         const int4 b = reinterpret_cast<const int4 *>(a.box)[k];
         const int32_t l = a.olabel[k];
         const int bh = b.z - b.x + 1, bw = b.w - b.y + 1;
         const int m = bh * bw;   // H * W <= 2^30
         if (m <= kWsSmemPx) {
-            for (int i = threadIdx.x; i < m; i += kThreads) {
+            for (int i = threadIdx.x; i < m; i += kWsThreads) {
                 const int y = i / bw, x = i - y * bw;
                 const int r = b.x + y, c = b.y + x;
                 const bool in = a.L[(int64_t)r * a.ld_L + c] == l;
@@ -593,13 +696,13 @@ __global__ void __launch_bounds__(kThreads) obj_watershed_kernel(ObjArgs a)
                 sv.d[i] = in ? a.D[(int64_t)r * a.ld_D + c] : 0;
             }
             __syncthreads();
-            watershed_object(sv, a, b.x, b.y, bh, bw, &red);
+            watershed_object(sv, g, a, b.x, b.y, bh, bw);
         } else {
             GlobalView gv{&a, l, b.x, b.y, bw};
-            for (int i = threadIdx.x; i < m; i += kThreads)
+            for (int i = threadIdx.x; i < m; i += kWsThreads)
                 if (gv.in(i)) a.nm[gv.pix(i)] = 0u;
             __syncthreads();
-            watershed_object(gv, a, b.x, b.y, bh, bw, &red);
+            watershed_object(gv, g, a, b.x, b.y, bh, bw);
         }
     }
 }
@@ -609,11 +712,14 @@ cudaError_t launch_watershed(const ObjArgs &a, int num_sms, cudaStream_t s, int 
     *launches = 0;
     cudaError_t e = launch_enumeration(a, s, launches);
     if (e != cudaSuccess) return e;
+    obj_classify_kernel<<<(unsigned)ceil_div(a.max_obj, 256), 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = cudaFuncSetAttribute(obj_watershed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemBytes);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid((const void *)obj_watershed_kernel, kWsSmemBytes, num_sms);
-    obj_watershed_kernel<<<(unsigned)grid, kThreads, kWsSmemBytes, s>>>(a);
-    *launches += 1;
+    obj_watershed_kernel<<<(unsigned)persistent_grid((const void *)obj_watershed_kernel, kWsSmemBytes, num_sms,
+                                                     kWsThreads),
+                           kWsThreads, kWsSmemBytes, s>>>(a);
+    *launches += 2;
     return cudaGetLastError();
 }
 

@@ -29,7 +29,10 @@ struct ObjArgs {
     int H, W;
     // workspace
     uint32_t *chunk_cnt;   // per chunk: objects whose first pixel lies in it, then their prefix sum
-    uint32_t *ctl;         // [0] objects, [1] next object of the per-object blocks, [2] basins
+    uint32_t *ctl;         // [0] objects, [1] next object of the per-object blocks, [2] basins,
+                           // [3] objects with a large box, [4] the others (watershed)
+    int32_t *order;        // watershed: objects by box size class (large first from the front, small
+                           // from the back)
     int32_t *idx_of;       // per pixel index (sparse): object index of the label it is the first pixel of
     int32_t *olabel;       // per object: label
     int32_t *box;          // per object: r0, c0, r1, c1
