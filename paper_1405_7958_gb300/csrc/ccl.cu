@@ -190,27 +190,47 @@ __device__ __forceinline__ bool local_labels(const UfImage &d, int bx, int by, i
 {
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = by * kB, c0 = bx * kB;
-    const int c = c0 + tx;
-    uint32_t any = 0;
+    // the block's row masks: thread t reads 4 adjacent pixels of row t / 8
+    // (one 32-bit load where aligned), eight threads combine a row's mask
+    {
+        const int rr = threadIdx.x >> 3, qq = threadIdx.x & 7;
+        const int gr = r0 + rr, gc = c0 + 4 * qq;
+        uint32_t nib = 0;
+        if (gr < d.H && gc < d.W) {
+            const uint8_t *px = d.in + (int64_t)gr * d.ld_in + gc;
+            if (gc + 3 < d.W && (reinterpret_cast<uintptr_t>(px) & 3u) == 0) {
+                const uint32_t v = *reinterpret_cast<const uint32_t *>(px);
+                nib = (uint32_t)((v & 0xffu) != 0) | (uint32_t)((v & 0xff00u) != 0) << 1 |
+                      (uint32_t)((v & 0xff0000u) != 0) << 2 | (uint32_t)((v & 0xff000000u) != 0) << 3;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (gc + k < d.W) nib |= (uint32_t)(px[k] != 0) << k;
+            }
+        }
+        uint32_t m = nib << (4 * qq);
+        m |= __shfl_xor_sync(0xffffffffu, m, 1);
+        m |= __shfl_xor_sync(0xffffffffu, m, 2);
+        m |= __shfl_xor_sync(0xffffffffu, m, 4);
+        if (qq == 0) M[rr] = m;
+        // a block without foreground (most of a sparse mask) has nothing to join
+        if (!__syncthreads_or(m != 0)) {
+#pragma unroll
+            for (int k = 0; k < kRowsPerThread; ++k) roots[k] = -1;
+            return false;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int lr = w * kRowsPerThread + k;
-        const int r = r0 + lr;
-        const bool f = (r < d.H && c < d.W) && d.in[(int64_t)r * d.ld_in + c] != 0;
-        const uint32_t m = __ballot_sync(0xffffffffu, f);
+        const uint32_t m = M[lr];
+        const bool f = (m >> tx) & 1u;
         const uint32_t starts = m & ~(m << 1);
-        if (tx == 0) M[lr] = m;
         int v = -1;
         if (f) v = lr * kB + (31 - __clz(starts & (0xffffffffu >> (31 - tx))));
         P[lr * kB + tx] = v;
-        any |= m;
     }
-    // a block without foreground (most of a sparse mask) has nothing to join
-    if (!__syncthreads_or(any != 0)) {
-#pragma unroll
-        for (int k = 0; k < kRowsPerThread; ++k) roots[k] = -1;
-        return false;
-    }
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) {
         const int lr = w * kRowsPerThread + k;
@@ -394,34 +414,57 @@ __global__ void __launch_bounds__(128) uf_roots_kernel(UfBatch b)
 
 // 4. labels with the area filter, from every pixel's local root (recorded
 // by stage 1); optionally the kept pixels as a bit plane (bit c % 32 of word
-// r * ceil(W / 32) + c / 32), which is all the distance transform needs
+// r * ceil(W / 32) + c / 32), which is all the distance transform needs.
+// A thread takes 4 adjacent pixels of one row (8 threads a block row), so
+// the labels leave in 16-byte stores where the row allows them.
 __global__ void __launch_bounds__(kThreads) uf_labels_kernel(UfBatch b)
 {
     const BlockRef br = find_block(b, blockIdx.x);
     const UfImage &d = *br.d;
-    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int r0 = br.by * kB, c0 = br.bx * kB, c = c0 + tx;
-    const int64_t wpr = ceil_div(d.W, 32);
+    const int q = threadIdx.x & 7, lr = threadIdx.x >> 3;
+    const int r = br.by * kB + lr, c = br.bx * kB + 4 * q;
     const bool empty = d.bempty[br.blk] != 0;
+    int32_t out[4] = {-1, -1, -1, -1};
+    const bool row_in = r < d.H;
+    if (row_in && !empty && c < d.W) {
+        const int64_t pix = (int64_t)r * d.W + c;
+        uint32_t lrs[4];
+        if ((d.W & 3) == 0) {   // 8-byte aligned: W and c are multiples of 4
+            const uint2 v = *reinterpret_cast<const uint2 *>(d.lroot + pix);
+            lrs[0] = v.x & 0xFFFFu, lrs[1] = v.x >> 16, lrs[2] = v.y & 0xFFFFu, lrs[3] = v.y >> 16;
+        } else {
 #pragma unroll
-    for (int k = 0; k < kRowsPerThread; ++k) {
-        const int r = r0 + w * kRowsPerThread + k;
-        const bool in = r < d.H && c < d.W;
-        const uint32_t lr = in && !empty ? d.lroot[(int64_t)r * d.W + c] : 0xFFFFu;
-        int32_t out = -1;
-        if (lr != 0xFFFFu) {
-            const int32_t root = d.U[global_index(d, br.bx, br.by, (int)lr)];
+            for (int k = 0; k < 4; ++k) lrs[k] = c + k < d.W ? d.lroot[pix + k] : 0xFFFFu;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (lrs[k] == 0xFFFFu) continue;
+            const int32_t root = d.U[global_index(d, br.bx, br.by, (int)lrs[k])];
             const int32_t area = d.A[root];
             if (area >= b.amin && area <= b.amax) {
-                out = root;
-                if (d.n_kept && root == (int32_t)((int64_t)r * d.W + c)) atomicAdd(d.n_kept, 1);
+                out[k] = root;
+                if (d.n_kept && root == (int32_t)(pix + k)) atomicAdd(d.n_kept, 1);
             }
         }
-        if (in) d.labels[(int64_t)r * d.ld_lab + c] = out;
-        if (d.fgbits) {
-            const uint32_t bits = __ballot_sync(0xffffffffu, out >= 0);
-            if (tx == 0 && r < d.H) d.fgbits[(int64_t)r * wpr + br.bx] = bits;
+    }
+    if (row_in && c < d.W) {
+        int32_t *dst = d.labels + (int64_t)r * d.ld_lab + c;
+        if (c + 3 < d.W && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+            *reinterpret_cast<int4 *>(dst) = make_int4(out[0], out[1], out[2], out[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c + k < d.W) dst[k] = out[k];
         }
+    }
+    if (d.fgbits) {
+        uint32_t bits = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bits |= (uint32_t)(out[k] >= 0) << (4 * q + k);
+        bits |= __shfl_xor_sync(0xffffffffu, bits, 1);
+        bits |= __shfl_xor_sync(0xffffffffu, bits, 2);
+        bits |= __shfl_xor_sync(0xffffffffu, bits, 4);
+        if (q == 0 && row_in) d.fgbits[(int64_t)r * ceil_div(d.W, 32) + br.bx] = bits;
     }
 }
 

@@ -129,6 +129,30 @@ __device__ __forceinline__ void edt_row_search(const uint16_t *sg, int W, bool a
     }
 }
 
+// The same search in 32-bit arithmetic (bit-plane path): sides are at most
+// 32768, so d^2 + g^2 < 2^31 is exact in unsigned 32 bits. Consecutive lanes
+// take consecutive columns (conflict-free 16-bit shared reads).
+__device__ __forceinline__ void edt_row_search32(const uint16_t *sg, int W, int32_t *out)
+{
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        const uint32_t gc = sg[c];
+        uint32_t best = gc == kInf ? 0xffffffffu : gc * gc;
+        for (uint32_t d = 1; d * d < best; ++d) {
+            const int cl = c - (int)d, cr = c + (int)d;
+            if (cl < 0 && cr >= W) break;
+            if (cl >= 0) {
+                const uint32_t g = sg[cl];
+                if (g != kInf) best = min(best, d * d + g * g);
+            }
+            if (cr < W) {
+                const uint32_t g = sg[cr];
+                if (g != kInf) best = min(best, d * d + g * g);
+            }
+        }
+        out[c] = best == 0xffffffffu ? -1 : (int32_t)best;
+    }
+}
+
 // CTA per row: exact minimum over columns with early termination
 __global__ void edt_row_kernel(EdtArgs a)
 {
@@ -311,7 +335,7 @@ __global__ void edt_row_bits_kernel(EdtBitsBatch b)
         }
     }
     __syncthreads();
-    edt_row_search(sg, a.W, true, a.d2 + (int64_t)r * a.ld_d2);
+    edt_row_search32(sg, a.W, a.d2 + (int64_t)r * a.ld_d2);
 }
 
 cudaError_t launch_edt_bits_batch(const EdtBitsBatch &b, cudaStream_t s)
