@@ -70,7 +70,9 @@ typedef enum {
     RT_EMARKER = 5,   /* marker above the mask somewhere (output still defined) */
     RT_EQUEUE = 6,    /* frontier queue overflow; never raised here: every queue of the
                          RT_QUEUE / RT_HYBRID visits has one slot per pixel of its tile and
-                         a pixel is queued at most once at a time */
+                         a pixel is queued at most once at a time, and a full RT_FRONTIER
+                         queue hands the propagation to the directional sweeps (same
+                         output) */
     RT_EUNAVAIL = 7,  /* requested variant or feature not available */
     RT_ESIZE = 8      /* image larger than the fixed scratch of rt_edt_noalloc */
 } rt_status;
@@ -80,7 +82,13 @@ enum {
     RT_AUTO = 0,    /* library choice (RT_RASTER) */
     RT_RASTER = 1,  /* directional sweeps of 32 x 64 tiles, revisiting flagged tiles */
     RT_QUEUE = 2,   /* per-tile pixel FIFOs (irregular wavefront propagation) */
-    RT_HYBRID = 3   /* one sweep visit of every tile, then pixel FIFOs for what remains */
+    RT_HYBRID = 3,  /* one sweep visit of every tile, then pixel FIFOs for what remains */
+    RT_FRONTIER = 4 /* one sweep visit of every tile, then global frontier queues of the
+                       pixels that can still grow: warp-ballot compacted seeding, persistent
+                       CTAs cascading through shared-memory queues with warp-aggregated
+                       appends, one grid barrier per global round. A full queue (or more than
+                       1022 rounds) hands over to the directional sweeps; batches of 2^21
+                       tiles of 32 x 64 or more run RT_HYBRID instead */
 };
 
 typedef struct rt_ctx rt_ctx;
@@ -99,6 +107,14 @@ RT_API rt_status rt_create(rt_ctx **ctx, int device, size_t workspace_bytes);
  * bound close to the need may or may not be reached); timeout_ms > 0 bounds
  * each propagation's device time (0: 20 s). Negative values: RT_EINVAL. */
 RT_API rt_status rt_set_limits(rt_ctx *ctx, int max_iters, int timeout_ms);
+
+/* Entries of each of the two global frontier queues of RT_FRONTIER on this
+ * context (4 bytes each, part of the workspace); 0 = one per pixel of the
+ * call's images padded to 32 x 64 tiles (the default). A smaller capacity
+ * bounds the workspace: a propagation whose queue fills up is finished by
+ * the directional sweeps, with the same output. Negative or above
+ * 2^32 - 1: RT_EINVAL. */
+RT_API rt_status rt_set_queue_capacity(rt_ctx *ctx, int64_t entries);
 
 /* Free a context and its workspace. Waits for the device first. NULL is a
  * no-op. */
@@ -130,7 +146,8 @@ RT_API rt_status rt_marker(rt_ctx *ctx, const uint8_t *mask, int64_t ld_mask,
  * where delta_conn is the maximum over a pixel and its conn-neighbours
  * (Vincent 1993). The paper runs it as an irregular wavefront propagation
  * (IWPP) over active elements; `variant` picks how the GPU propagates
- * (RT_RASTER, RT_QUEUE, RT_HYBRID, or RT_AUTO), with identical results.
+ * (RT_RASTER, RT_QUEUE, RT_HYBRID, RT_FRONTIER, or RT_AUTO), with identical
+ * results.
  *
  * marker: uint8 H x W (ld_marker), or NULL: then the marker is derived on
  *         the fly as in rt_marker with `h_offset`.
@@ -421,7 +438,8 @@ typedef struct {
     int conn_recon;  /* connectivity of the reconstruction (8) */
     int conn_fill;   /* connectivity of the background flood in fill-holes (4) */
     int variant;     /* reconstruction variant for every tile (RT_AUTO) */
-    int max_local;   /* sweep iterations per dense tile visit; 0 = default (12; RT_HYBRID 64) */
+    int max_local;   /* sweep iterations per dense tile visit; 0 = default (12; RT_HYBRID and
+                        RT_FRONTIER 64) */
     int policy;      /* RT_POLICY_PLAIN: `variant` and `max_local` for every tile;
                         RT_POLICY_LEARNED: the attached picker chooses a schedule per tile
                         (rt_set_picker_classes), and the plain schedule is kept whenever no
@@ -457,10 +475,13 @@ RT_API rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, cons
                            void *stream);
 
 /* Device workspace bytes rt_segment_batch needs for these tiles and
- * parameters (its largest chunk of up to 32 tiles): a context created with
- * at least this much never allocates during such a call. 0 on invalid
- * arguments. Host-only; the tiles' pointers are not read. */
-RT_API size_t rt_segment_workspace_bytes(const rt_tile *tiles, int n, const rt_seg_params *params);
+ * parameters (its largest chunk of up to 32 tiles) on context `ctx`, whose
+ * picker classes and frontier-queue capacity count (NULL: the defaults): a
+ * context created with at least this much never allocates during such a
+ * call. 0 on invalid arguments. Host-only; the tiles' pointers are not
+ * read. */
+RT_API size_t rt_segment_workspace_bytes(const rt_ctx *ctx, const rt_tile *tiles, int n,
+                                         const rt_seg_params *params);
 
 #ifdef __cplusplus
 }

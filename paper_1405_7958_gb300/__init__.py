@@ -18,12 +18,12 @@ from dataclasses import dataclass
 import torch
 
 from . import _native
-from ._native import (RT_AUTO, RT_EINVAL, RT_EMARKER, RT_ETIMEOUT, RT_EUNAVAIL, RT_HYBRID, RT_OK,  # noqa: F401
-                      RT_QUEUE, RT_RASTER)
+from ._native import (RT_AUTO, RT_EINVAL, RT_EMARKER, RT_ETIMEOUT, RT_EUNAVAIL, RT_FRONTIER, RT_HYBRID,  # noqa: F401
+                      RT_OK, RT_QUEUE, RT_RASTER)
 
 __all__ = [
     "Context", "SegParams", "marker", "reconstruct", "fill_holes", "label_area", "edt",
-    "segment_batch", "RT_AUTO", "RT_RASTER", "RT_QUEUE", "RT_HYBRID",
+    "segment_batch", "RT_AUTO", "RT_RASTER", "RT_QUEUE", "RT_HYBRID", "RT_FRONTIER",
 ]
 
 _lib = None
@@ -87,6 +87,12 @@ class Context:
         """Bounds of the propagations of the single-operation calls (and the
         defaults of segment_batch): tile visits per tile, device time."""
         _check(lib().rt_set_limits(self._h, int(max_iters), int(timeout_ms)), "rt_set_limits")
+
+    def set_queue_capacity(self, entries: int = 0):
+        """Entries of each global frontier queue of RT_FRONTIER (0: one per
+        padded pixel of the call's images). A full queue hands over to the
+        directional sweeps, with the same output."""
+        _check(lib().rt_set_queue_capacity(self._h, int(entries)), "rt_set_queue_capacity")
 
     def timing(self, enable: bool = True):
         _check(lib().rt_timing_enable(self._h, int(enable)), "rt_timing_enable")
@@ -395,9 +401,10 @@ class SegParams:
         return p
 
 
-def segment_workspace_bytes(shapes, params: SegParams | None = None) -> int:
+def segment_workspace_bytes(shapes, params: SegParams | None = None, ctx: Context | None = None) -> int:
     """Device workspace bytes segment_batch needs for tiles of these (H, W)
-    shapes (the library's exact figure, rt_segment_workspace_bytes)."""
+    shapes on `ctx` (its picker classes and frontier-queue capacity; None:
+    the defaults) -- the library's exact figure, rt_segment_workspace_bytes."""
     n = len(shapes)
     if n == 0:
         return 0
@@ -408,7 +415,7 @@ def segment_workspace_bytes(shapes, params: SegParams | None = None) -> int:
         t.img = t.labels = t.d2 = 1            # placeholders: the size query reads no pointer
         t.ld_img = t.ld_labels = t.ld_d2 = int(W)
     cp = (params or SegParams()).to_c()
-    return int(lib().rt_segment_workspace_bytes(tiles, n, ctypes.byref(cp)))
+    return int(lib().rt_segment_workspace_bytes(ctx._h if ctx is not None else None, tiles, n, ctypes.byref(cp)))
 
 
 def segment_batch(images, params: SegParams | None = None, *, outputs=None, want_recon: bool = True,

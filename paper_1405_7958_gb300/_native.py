@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librtseg.so")
 
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT, RT_EMARKER, RT_EQUEUE, RT_EUNAVAIL, RT_ESIZE = range(9)
-RT_AUTO, RT_RASTER, RT_QUEUE, RT_HYBRID = range(4)
+RT_AUTO, RT_RASTER, RT_QUEUE, RT_HYBRID, RT_FRONTIER = range(5)
 
 # every symbol declared in include/rt.h
 EXPORTS = (
@@ -20,7 +20,7 @@ EXPORTS = (
     "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_recon_stats",
     "rt_edt_noalloc", "rt_synth_tile", "rt_tile_features", "rt_mlp_forward", "rt_mlp_backward",
     "rt_mlp_adamw", "rt_set_picker", "rt_last_picks", "rt_set_limits", "rt_segment_workspace_bytes",
-    "rt_feature_norm", "rt_watershed", "rt_object_features", "rt_set_picker_classes",
+    "rt_feature_norm", "rt_watershed", "rt_object_features", "rt_set_picker_classes", "rt_set_queue_capacity",
 )
 RT_NPHASES = 9
 PHASES = ("recon_init", "recon_sweep", "recon_out", "fill", "label", "edt", "pick", "objects", "watershed")
@@ -106,8 +106,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_seg_params_default.restype = None
     lib.rt_segment_batch.argtypes = [_vp, ctypes.POINTER(RtTile), _int, ctypes.POINTER(RtSegParams), _vp]
     lib.rt_segment_batch.restype = _int
-    lib.rt_segment_workspace_bytes.argtypes = [ctypes.POINTER(RtTile), _int, ctypes.POINTER(RtSegParams)]
+    lib.rt_segment_workspace_bytes.argtypes = [_vp, ctypes.POINTER(RtTile), _int, ctypes.POINTER(RtSegParams)]
     lib.rt_segment_workspace_bytes.restype = ctypes.c_size_t
+    lib.rt_set_queue_capacity.argtypes = [_vp, _i64]
+    lib.rt_set_queue_capacity.restype = _int
     lib.rt_feature_norm.argtypes = [_vp, _vp, _int, _vp, _vp]
     lib.rt_feature_norm.restype = _int
     lib.rt_timing_enable.argtypes = [_vp, _int]

@@ -1,7 +1,8 @@
 """Autotuner for the batched segmentation chain.
 
-The run-time knobs of the reconstruction are the propagation variant and the
-budget of sweep iterations per dense tile visit (`max_local`): a small
+The run-time knobs of the reconstruction are the propagation variant (the
+raster sweeps, the hybrid's per-tile queues, the global frontier queues)
+and the budget of sweep iterations per dense tile visit (`max_local`): a small
 budget revisits tiles more often, a large one sweeps tiles longer before
 their neighbours' news arrives. The tuner times each candidate on the batch
 itself (CUDA events on the launch stream, median of `reps`), keeps the
@@ -17,7 +18,7 @@ import torch
 
 import paper_1405_7958_gb300 as rt
 
-CANDIDATES = tuple((v, m) for v in (rt.RT_RASTER,) for m in (4, 8, 12, 16)) + ((rt.RT_HYBRID, 0),)
+CANDIDATES = tuple((v, m) for v in (rt.RT_RASTER,) for m in (4, 8, 12, 16)) + ((rt.RT_HYBRID, 0), (rt.RT_FRONTIER, 0))
 
 
 def size_class(images) -> str:

@@ -40,6 +40,7 @@ struct rt_ctx {
     PickTable classes{{0, 0, 0, 0}, {4, 12, 24, 12}};   // picker classes (rt_set_picker_classes); entry 3 per call
     int max_iters = 0;                     // limits of the single-operation entry points (rt_set_limits)
     uint64_t timeout_ns = 0;
+    int64_t fq_cap = 0;                    // entries per global frontier queue (0: one per padded pixel)
     std::vector<PhaseRec> recs;
     std::vector<cudaEvent_t> pool;
 };
@@ -157,15 +158,45 @@ struct ReconWs {
     uint32_t *ctl;     // kCtlWords control words (recon.cuh)
     int32_t *err;
     int32_t *map;      // kGroups x ntiles tile lists when the variant is chosen per image
+    uint32_t *fq[2];   // RT_FRONTIER: global frontier queues (fq_cap entries each), or null
+    uint32_t *fctl;    //              their kFqCtlWords control words
+    uint32_t fq_cap;
 };
 
-// Reserve the sweep control block and per-image padded buffers.
-void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w, bool grouped = false)
+// Whether a call runs RT_FRONTIER somewhere: as its variant, or as one of
+// the picker's classes under the learned policy (ctx NULL: the default
+// classes, all RT_RASTER).
+bool uses_frontier(const rt_ctx *ctx, int variant, bool learned)
+{
+    if (variant == RT_FRONTIER) return true;
+    if (!learned || !ctx) return false;
+    for (int c = 0; c < kPickClasses; ++c)
+        if (ctx->classes.group[c] == RT_FRONTIER - RT_RASTER) return true;
+    return false;
+}
+
+// Entries of each global frontier queue for batch b: the context's setting,
+// else one per padded pixel of the batch.
+uint32_t frontier_capacity(const rt_ctx *ctx, const ReconBatch &b)
+{
+    int64_t px = 0;
+    for (int i = 0; i < b.n; ++i) px += (int64_t)b.img[i].Hp * b.img[i].Wp;
+    const int64_t cap = ctx && ctx->fq_cap > 0 ? ctx->fq_cap : px;
+    return (uint32_t)(cap < 0xffffffffLL ? cap : 0xffffffffLL);
+}
+
+// Reserve the sweep control block and per-image padded buffers (and the
+// global frontier queues when fq_cap > 0).
+void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w, bool grouped = false, uint32_t fq_cap = 0)
 {
     w.flags = cv.take<uint32_t>((size_t)b.ntiles);
     w.ctl = cv.take<uint32_t>(kCtlWords);
     w.err = cv.take<int32_t>(1);
     w.map = grouped ? cv.take<int32_t>((size_t)kGroups * b.ntiles) : nullptr;
+    w.fq_cap = fq_cap;
+    w.fq[0] = fq_cap ? cv.take<uint32_t>(fq_cap) : nullptr;
+    w.fq[1] = fq_cap ? cv.take<uint32_t>(fq_cap) : nullptr;
+    w.fctl = fq_cap ? cv.take<uint32_t>(kFqCtlWords) : nullptr;
     for (int i = 0; i < b.n; ++i) {
         ReconImage &d = b.img[i];
         d.Rw = cv.take<uint8_t>((size_t)d.Hp * d.Wp);
@@ -187,7 +218,7 @@ struct Limits {
 
 Limits ctx_limits(const rt_ctx *ctx) { return {ctx->max_iters, ctx->timeout_ns ? ctx->timeout_ns : kSweepTimeoutNs}; }
 
-int default_max_local(int variant) { return variant == RT_HYBRID ? 64 : 12; }
+int default_max_local(int variant) { return variant == RT_HYBRID || variant == RT_FRONTIER ? 64 : 12; }
 
 rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int variant, int max_local, int32_t *err,
                     cudaStream_t s, Limits lim, const int32_t *pick = nullptr)
@@ -198,6 +229,13 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
     PickTable table = ctx->classes;
     table.group[kPickClasses] = variant - RT_RASTER;
     table.max_local[kPickClasses] = max_local > 0 ? max_local : default_max_local(variant);
+    // A frontier entry names its tile in 21 bits, and the queues need their
+    // workspace: without either, frontier schedules run as RT_HYBRID (the
+    // same dense first pass, then per-tile queues; same output).
+    const bool fq_ok = w.fq_cap > 0 && b.ntiles < kFqMaxTiles;
+    for (int e = 0; e < kPickEntries; ++e)
+        if (table.group[e] == RT_FRONTIER - RT_RASTER && !fq_ok) table.group[e] = RT_HYBRID - RT_RASTER;
+    if (variant == RT_FRONTIER && !fq_ok) variant = RT_HYBRID;
     // The picker learned its budgets on lone tiles, where a tile's latency
     // sets the time and short visits can win. Tiles that share a launch with
     // others are bound by its throughput instead, and there budgets below
@@ -209,9 +247,9 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
             if (table.group[c] == 0 && table.max_local[c] < plain_raster) table.max_local[c] = plain_raster;
     }
     // RT_RASTER / RT_QUEUE: every tile starts flagged for a dense visit (the
-    // queue visit then seeds every pixel); RT_HYBRID: nothing flagged, the
-    // dense pass over all tiles flags what remains.
-    const uint32_t flag0 = variant == RT_HYBRID ? 0u : 2u;
+    // queue visit then seeds every pixel); RT_HYBRID / RT_FRONTIER: nothing
+    // flagged, the dense pass over all tiles flags what remains.
+    const uint32_t flag0 = variant == RT_HYBRID || variant == RT_FRONTIER ? 0u : 2u;
     RT_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, kCtlWords * sizeof(uint32_t), s));
     {
         Phase ph(ctx, RT_PHASE_RECON_INIT, s);
@@ -235,9 +273,13 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
     p.nvirt = nullptr;
     p.pick = pick;
     p.table = table;
+    p.fq[0] = w.fq[0];
+    p.fq[1] = w.fq[1];
+    p.fq_cap = w.fq_cap;
+    p.fctl = w.fctl;
     int grid = 0;
     Phase ph(ctx, RT_PHASE_RECON_SWEEP, s);
-    bool used[kGroups] = {false, false, false};   // groups some schedule of the table propagates in
+    bool used[kGroups] = {false, false, false, false};   // groups some schedule of the table propagates in
     for (int e = 0; e < kPickEntries; ++e)
         if (table.group[e] >= 0 && table.group[e] < kGroups) used[table.group[e]] = true;
     for (int g = 0; g < (pick ? kGroups : 1); ++g) {
@@ -249,12 +291,23 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
             p.pending = w.ctl + kCtlGroupPending + g;
         }
         p.max_local = max_local > 0 ? max_local : default_max_local(v);
-        if (v == RT_HYBRID) {
+        if (v == RT_HYBRID || v == RT_FRONTIER) {
             RT_CUDA_TRY(launch_recon_dense(p, conn, s));
             ctx->launches += 1;
         }
+        if (v == RT_FRONTIER) {
+            // seed and drain the global frontier queues; the directional
+            // sweeps that follow find nothing flagged unless a queue
+            // overflowed
+            RT_CUDA_TRY(cudaMemsetAsync(w.fctl, 0, kFqCtlWords * sizeof(uint32_t), s));
+            RT_CUDA_TRY(launch_recon_seed(p, conn, s));
+            RT_CUDA_TRY(launch_recon_frontier(p, conn, ctx->num_sms, s, &grid));
+            ctx->launches += 2;
+            p.max_local = max_local > 0 ? max_local : default_max_local(RT_RASTER);
+        }
         ctx->launches += 1;
-        RT_CUDA_TRY(launch_recon_persistent(p, conn, v == RT_RASTER ? 0 : 1, ctx->num_sms, s, &grid));
+        RT_CUDA_TRY(launch_recon_persistent(p, conn, v == RT_RASTER || v == RT_FRONTIER ? 0 : 1, ctx->num_sms, s,
+                                            &grid));
     }
     return RT_OK;
 }
@@ -291,7 +344,7 @@ bool bad_params(const rt_seg_params &P)
     if (P.conn_recon != 4 && P.conn_recon != 8) return true;
     if (P.conn_fill != 4 && P.conn_fill != 8) return true;
     if (P.h_offset < 0 || P.h_offset > 255 || P.threshold < 0 || P.threshold > 256) return true;
-    if (P.variant < RT_AUTO || P.variant > RT_HYBRID) return true;
+    if (P.variant < RT_AUTO || P.variant > RT_FRONTIER) return true;
     if (P.policy != RT_POLICY_PLAIN && P.policy != RT_POLICY_LEARNED) return true;
     if (P.max_local < 0 || P.max_iters < 0 || P.timeout_ms < 0) return true;
     if (P.pick_min_prob < 0 || P.pick_min_prob > 1000) return true;
@@ -326,7 +379,8 @@ struct Chunk {
 
 // Lays chunk [c0, c0 + cn) out in cv. With cv.base == nullptr only the size
 // is measured (cv.off); no pointer is formed.
-void layout_chunk(Carve &cv, Chunk &c, const rt_tile *tiles, int c0, int cn, const rt_seg_params &P, bool learned)
+void layout_chunk(Carve &cv, Chunk &c, const rt_tile *tiles, int c0, int cn, const rt_seg_params &P, bool learned,
+                  const rt_ctx *ctx)
 {
     const bool real = cv.base != nullptr;
     std::memset(&c.b, 0, sizeof(c.b));
@@ -334,7 +388,8 @@ void layout_chunk(Carve &cv, Chunk &c, const rt_tile *tiles, int c0, int cn, con
         const rt_tile &t = tiles[c0 + i];
         add_image(c.b, nullptr, 0, t.img, t.ld_img, t.H, t.W, P.h_offset);
     }
-    carve_recon(cv, c.b, c.w, learned);
+    carve_recon(cv, c.b, c.w, learned,
+                uses_frontier(ctx, P.variant, learned) ? frontier_capacity(ctx, c.b) : 0u);
     if (learned) {
         c.fb.n = cn;
         for (int i = 0; i < cn; ++i) {
@@ -396,14 +451,14 @@ void layout_chunk(Carve &cv, Chunk &c, const rt_tile *tiles, int c0, int cn, con
 }
 
 // Workspace bytes rt_segment_batch needs for these tiles (the largest chunk).
-size_t segment_ws_bytes(const rt_tile *tiles, int n, const rt_seg_params &P, bool learned)
+size_t segment_ws_bytes(const rt_tile *tiles, int n, const rt_seg_params &P, bool learned, const rt_ctx *ctx)
 {
     size_t most = 0;
     for (int c0 = 0; c0 < n; c0 += kMaxImgs) {
         const int cn = n - c0 < kMaxImgs ? n - c0 : kMaxImgs;
         Carve cv;
         Chunk c;
-        layout_chunk(cv, c, tiles, c0, cn, P, learned);
+        layout_chunk(cv, c, tiles, c0, cn, P, learned, ctx);
         most = cv.off > most ? cv.off : most;
     }
     return most;
@@ -414,7 +469,7 @@ size_t segment_ws_bytes(const rt_tile *tiles, int n, const rt_seg_params &P, boo
 // ================================================================= C ABI
 extern "C" {
 
-int rt_version(void) { return 200; }
+int rt_version(void) { return 201; }
 
 const char *rt_status_str(int status)
 {
@@ -471,12 +526,19 @@ rt_status rt_set_limits(rt_ctx *ctx, int max_iters, int timeout_ms)
     return RT_OK;
 }
 
-size_t rt_segment_workspace_bytes(const rt_tile *tiles, int n, const rt_seg_params *params)
+size_t rt_segment_workspace_bytes(const rt_ctx *ctx, const rt_tile *tiles, int n, const rt_seg_params *params)
 {
     if ((!tiles && n > 0) || n < 0 || !params || bad_params(*params)) return 0;
     for (int i = 0; i < n; ++i)
         if (bad_tile(tiles[i])) return 0;
-    return segment_ws_bytes(tiles, n, *params, params->policy == RT_POLICY_LEARNED);
+    return segment_ws_bytes(tiles, n, *params, params->policy == RT_POLICY_LEARNED, ctx);
+}
+
+rt_status rt_set_queue_capacity(rt_ctx *ctx, int64_t entries)
+{
+    if (!ctx || entries < 0 || entries > 0xffffffffLL) return RT_EINVAL;
+    ctx->fq_cap = entries;
+    return RT_OK;
 }
 
 void rt_destroy(rt_ctx *ctx)
@@ -573,7 +635,7 @@ rt_status rt_reconstruct(rt_ctx *ctx, const uint8_t *marker, int64_t ld_marker, 
 {
     if (!ctx || !mask || !out || bad_dims(H, W) || ld_mask < W || ld_out < W) return RT_EINVAL;
     if (conn != 4 && conn != 8) return RT_EINVAL;
-    if (variant < RT_AUTO || variant > RT_HYBRID) return RT_EINVAL;
+    if (variant < RT_AUTO || variant > RT_FRONTIER) return RT_EINVAL;
     if (marker && ld_marker < W) return RT_EINVAL;
     if (!marker && (h_offset < 0 || h_offset > 255)) return RT_EINVAL;
     if (overlaps(out, span(H, ld_out, 1, W), mask, span(H, ld_mask, 1, W))) return RT_EINVAL;
@@ -586,14 +648,15 @@ rt_status rt_reconstruct(rt_ctx *ctx, const uint8_t *marker, int64_t ld_marker, 
     ReconBatch b;
     std::memset(&b, 0, sizeof(b));
     add_image(b, marker, ld_marker, mask, ld_mask, H, W, h_offset);
+    const uint32_t fq_cap = variant == RT_FRONTIER ? frontier_capacity(ctx, b) : 0u;
     Carve cv;
     ReconWs w;
-    carve_recon(cv, b, w);
+    carve_recon(cv, b, w, false, fq_cap);
     rt_status st = ensure_ws(ctx, cv.off);
     if (st != RT_OK) return st;
     cv = Carve();
     cv.base = (char *)ctx->ws;
-    carve_recon(cv, b, w);
+    carve_recon(cv, b, w, false, fq_cap);
 
     int32_t *err = dev_status ? dev_status : w.err;
     RT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
@@ -851,7 +914,7 @@ rt_status rt_set_picker_classes(rt_ctx *ctx, const int *variants, const int *max
     PickTable t = ctx->classes;
     for (int c = 0; c < kPickClasses; ++c) {
         const int v = variants[c] == RT_AUTO ? RT_RASTER : variants[c];
-        if (v < RT_RASTER || v > RT_HYBRID || max_locals[c] < 0) return RT_EINVAL;
+        if (v < RT_RASTER || v > RT_FRONTIER || max_locals[c] < 0) return RT_EINVAL;
         t.group[c] = v - RT_RASTER;
         t.max_local[c] = max_locals[c] > 0 ? max_locals[c] : default_max_local(v);
     }
@@ -947,7 +1010,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
     if (P.max_iters > 0) lim.max_iters = P.max_iters;
     if (P.timeout_ms > 0) lim.timeout_ns = (uint64_t)P.timeout_ms * 1000000ull;
     // one allocation for the largest chunk, before anything is enqueued
-    rt_status st = ensure_ws(ctx, segment_ws_bytes(tiles, n, P, learned));
+    rt_status st = ensure_ws(ctx, segment_ws_bytes(tiles, n, P, learned, ctx));
     if (st != RT_OK) return st;
 
     for (int c0 = 0; c0 < n; c0 += kMaxImgs) {
@@ -955,7 +1018,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         Chunk c;
         Carve cv;
         cv.base = (char *)ctx->ws;
-        layout_chunk(cv, c, tiles, c0, cn, P, learned);
+        layout_chunk(cv, c, tiles, c0, cn, P, learned, ctx);
         RT_CUDA_TRY(cudaMemsetAsync(c.w.err, 0, sizeof(int32_t), s));
         if (!learned) {
             st = run_recon(ctx, c.b, c.w, P.conn_recon, P.variant, P.max_local, c.w.err, s, lim);

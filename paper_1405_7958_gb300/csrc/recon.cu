@@ -23,7 +23,11 @@
 //     tiles until no tile is flagged or being visited (no grid barrier).
 // RT_RASTER = dense visits only; RT_QUEUE = queue visits only, every tile
 // seeded with all its pixels; RT_HYBRID = one dense visit of every tile,
-// then queue visits for the tiles whose halo changed.
+// then queue visits for the tiles whose halo changed; RT_FRONTIER = one
+// dense visit of every tile, then the active pixels of the whole batch in
+// global frontier queues: seeded with warp-ballot compaction, drained by
+// persistent CTAs that cascade through shared-memory queues with
+// warp-aggregated appends and spill to the global queue of the next round.
 #include "recon.cuh"
 
 namespace rtk {
@@ -86,17 +90,17 @@ __global__ void recon_init_kernel(const ReconBatch b, uint32_t *flags, uint32_t 
             for (int j = 0; j < i; ++j)
                 if (pick_group(pick, table, j) == g) off += b.img[j].tiles_x * b.img[j].tiles_y;
             int32_t *mg = map + (int64_t)g * b.ntiles + off;
-            const uint32_t f0 = g == 2 ? 0u : 2u;
+            const uint32_t f0 = g >= 2 ? 0u : 2u;   // hybrid, frontier: the dense pass flags
             for (int k = tid; k < nt; k += nth) {
                 flags[d.tile_base + k] = f0;
                 mg[k] = d.tile_base + k;
             }
             if (i == 0 && tid == 0) {
-                uint32_t cnt[kGroups] = {0u, 0u, 0u};
+                uint32_t cnt[kGroups] = {0u, 0u, 0u, 0u};
                 for (int j = 0; j < b.n; ++j) cnt[pick_group(pick, table, j)] += b.img[j].tiles_x * b.img[j].tiles_y;
                 for (int q = 0; q < kGroups; ++q) {
                     ctl[kCtlGroupCount + q] = cnt[q];
-                    ctl[kCtlGroupPending + q] = q == 2 ? 0u : cnt[q];
+                    ctl[kCtlGroupPending + q] = q >= 2 ? 0u : cnt[q];
                 }
             }
         }
@@ -637,6 +641,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_dense_kernel(SweepPar
     wb.sHR = wb.sHL + (kTH + 2);
     wb.sR0 = reinterpret_cast<uint16_t *>(wb.sHR + (kTH + 2));
     const uint32_t it = visit_tile<CONN>(p, t, wb, lane);
+    if (lane == 0 && p.max_visits) atomicAdd(p.spent, 1u);   // one visit per tile: within any bound
     if (lane == 0 && p.visits) {
         atomicAdd(p.visits, 1u);
         atomicAdd(p.visits + 1, it);
@@ -783,6 +788,407 @@ cudaError_t launch_recon_persistent(const SweepParams &p, int conn, int queue, i
     SweepParams pp = p;
     void *args[] = {&pp};
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kWarpsPerCta * 32), args, smem, s);
+}
+
+// ------------------------------------------------------ global frontier
+// Entry of the frontier queues: tile << 11 | row << 6 | column (row, column
+// within the 32 x 64 tile).
+__device__ __forceinline__ uint32_t fq_entry(int t, int r, int c)
+{
+    return ((uint32_t)t << 11) | ((uint32_t)r << 6) | (uint32_t)c;
+}
+
+// Image, padded row and column of tile t's pixel (r, c).
+struct FqPixel {
+    int img, row, col;
+};
+__device__ __forceinline__ FqPixel fq_decode(const SweepParams &p, uint32_t e)
+{
+    const int t = (int)(e >> 11);
+    FqPixel q;
+    q.img = find_image(p, t);
+    const ReconImage &d = p.b.img[q.img];
+    const int lt = t - d.tile_base;
+    const int tx = lt / d.tiles_y, ty = lt - tx * d.tiles_y;
+    q.row = ty * kTH + (int)((e >> 6) & 31u);
+    q.col = tx * kTW + (int)(e & 63u);
+    return q;
+}
+
+// Raises byte *a to v if that is larger (a 32-bit compare-and-swap on the
+// word holding it; every other writer of the word during the drain does the
+// same). Returns true if this call raised it. Bytes only grow, so the loop
+// retries at most once per increase of one of the word's four bytes.
+__device__ __forceinline__ bool fq_raise(uint8_t *a, uint32_t v)
+{
+    uint32_t *w = reinterpret_cast<uint32_t *>(reinterpret_cast<uintptr_t>(a) & ~uintptr_t(3));
+    const uint32_t sh = 8u * (uint32_t)(reinterpret_cast<uintptr_t>(a) & 3u);
+    uint32_t old = __ldcg(w);
+    while (((old >> sh) & 0xffu) < v) {
+        const uint32_t nw = (old & ~(0xffu << sh)) | (v << sh);
+        const uint32_t prev = atomicCAS(w, old, nw);
+        if (prev == old) return true;
+        old = prev;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+// Seeding: one warp per tile of the launch that the dense visits left
+// flagged. The tile and its one-pixel halo are read into shared memory; every
+// pixel is raised once to min(I, maximum of its neighbours) where that is
+// larger, and the raised pixels are appended to fq[0] (one atomic per warp).
+// Unflagged tiles need nothing: their visit reached the local fixed point and
+// no neighbour changed their halo since, so the only pixels that can still
+// grow lie in flagged tiles or next to pixels raised here, which the queue
+// holds.
+constexpr int kSeedWarps = 4;
+constexpr int kSeedW = kTW + 4;   // shared row: column c at index c + 1
+template <int CONN>
+__global__ void __launch_bounds__(kSeedWarps * 32) recon_seed_kernel(SweepParams p)
+{
+    __shared__ uint8_t sR[kSeedWarps][kTH + 2][kSeedW];
+    __shared__ uint8_t sI[kSeedWarps][kTH][kTW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int v = blockIdx.x * kSeedWarps + warp;
+    const int n = p.nvirt ? (int)*p.nvirt : p.ntiles;
+    if (v >= n) return;
+    const int t = p.map ? p.map[v] : v;
+    uint32_t f = 0;
+    if (lane == 0) f = atomicExch(p.flags + t, 0u);
+    if (__shfl_sync(0xffffffffu, f, 0) == 0u) return;
+    const int img = find_image(p, t);
+    const ReconImage &d = p.b.img[img];
+    const int lt = t - d.tile_base;
+    const int tx = lt / d.tiles_y, ty = lt - tx * d.tiles_y;
+    const int r0 = ty * kTH, c0 = tx * kTW;
+    const int64_t Wp = d.Wp;
+    uint8_t (*R)[kSeedW] = sR[warp];
+    uint8_t (*I)[kTW] = sI[warp];
+    for (int rr = -1; rr <= kTH; ++rr) {
+        const int gr = r0 + rr;
+        const bool in = gr >= 0 && gr < d.Hp;
+        uint32_t pr = 0;
+        if (in) pr = __ldcg(reinterpret_cast<const uint16_t *>(d.Rw + gr * Wp + c0) + lane);
+        R[rr + 1][2 * lane + 1] = (uint8_t)pr;
+        R[rr + 1][2 * lane + 2] = (uint8_t)(pr >> 8);
+        if (lane < 2) {
+            const int gc = lane ? c0 + kTW : c0 - 1;
+            R[rr + 1][lane ? kTW + 1 : 0] = (in && gc >= 0 && gc < d.Wp) ? __ldcg(d.Rw + gr * Wp + gc) : (uint8_t)0;
+        }
+        if (rr >= 0 && rr < kTH) {
+            const uint32_t pi = __ldg(reinterpret_cast<const uint16_t *>(d.Iw + gr * Wp + c0) + lane);
+            I[rr][2 * lane] = (uint8_t)pi;
+            I[rr][2 * lane + 1] = (uint8_t)(pi >> 8);
+        }
+    }
+    __syncwarp();
+    uint64_t bits = 0;   // bit 2 r + k: pixel (r, 2 lane + k) was raised
+    for (int r = 0; r < kTH; ++r) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int c = 2 * lane + k;       // shared column c + 1
+            uint32_t m = max(max((uint32_t)R[r][c + 1], (uint32_t)R[r + 2][c + 1]),
+                             max((uint32_t)R[r + 1][c], (uint32_t)R[r + 1][c + 2]));
+            if (CONN == 8)
+                m = max(m, max(max((uint32_t)R[r][c], (uint32_t)R[r][c + 2]),
+                               max((uint32_t)R[r + 2][c], (uint32_t)R[r + 2][c + 2])));
+            const uint32_t nv = min(m, (uint32_t)I[r][c]);
+            if (nv > R[r + 1][c + 1]) {
+                d.Rw[(int64_t)(r0 + r) * Wp + c0 + c] = (uint8_t)nv;
+                bits |= 1ull << (2 * r + k);
+            }
+        }
+    }
+    // append: an inclusive warp scan of the counts, one atomic per warp
+    const uint32_t cnt = (uint32_t)__popcll(bits);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0u) return;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(p.fctl + kFqTail, total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    uint32_t pos = base + incl - cnt;
+    bool over = false;
+    while (bits) {
+        const int b = __ffsll((long long)bits) - 1;
+        bits &= bits - 1;
+        if (pos < p.fq_cap) p.fq[0][pos] = fq_entry(t, b >> 1, 2 * lane + (b & 1));
+        else over = true;
+        ++pos;
+    }
+    if (over) atomicExch(p.fctl + kFqOver, 1u);
+}
+
+cudaError_t launch_recon_seed(const SweepParams &p, int conn, cudaStream_t s)
+{
+    const dim3 grid((unsigned)ceil_div(p.ntiles, kSeedWarps));
+    if (conn == 8) recon_seed_kernel<8><<<grid, kSeedWarps * 32, 0, s>>>(p);
+    else recon_seed_kernel<4><<<grid, kSeedWarps * 32, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+constexpr int kFqThreads = 256;
+constexpr int kFqLocal = 2048;   // entries per shared-memory queue
+constexpr int kFqGrab = 1024;    // entries a CTA takes from a global queue at a time
+
+// Appends the lanes' raised pixels: into the CTA's next shared queue through
+// one shared atomic per warp, and what does not fit into the global queue of
+// the next round through one global atomic per warp. Called by all 32 lanes.
+__device__ __forceinline__ void fq_push(const SweepParams &p, bool raised, uint32_t e, uint32_t *next,
+                                        uint32_t *cnt, uint32_t *out, uint32_t *out_tail, int lane)
+{
+    const uint32_t m = __ballot_sync(0xffffffffu, raised);
+    if (m == 0u) return;
+    const int lead = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == lead) base = atomicAdd(cnt, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    const uint32_t slot = base + (uint32_t)__popc(m & lanemask_lt(lane));
+    const bool spill = raised && slot >= (uint32_t)kFqLocal;
+    if (raised && !spill) next[slot] = e;
+    const uint32_t sm = __ballot_sync(0xffffffffu, spill);
+    if (sm == 0u) return;
+    const int l2 = __ffs(sm) - 1;
+    uint32_t gb = 0;
+    if (lane == l2) gb = atomicAdd(out_tail, (uint32_t)__popc(sm));
+    gb = __shfl_sync(0xffffffffu, gb, l2);
+    if (spill) {
+        const uint32_t g = gb + (uint32_t)__popc(sm & lanemask_lt(lane));
+        if (g < p.fq_cap) out[g] = e;
+        else atomicExch(p.fctl + kFqOver, 1u);
+    }
+}
+
+// Pops one entry per lane (valid lanes): reads the pixel's current value v
+// and raises each neighbour q to min(v, I(q)) where that is larger, queueing
+// the neighbours it raised. The pixel's value and all neighbours' I and R are
+// loaded together (one round trip to L2), then the raises (compare-and-swap),
+// then the appends. Called by all 32 lanes.
+template <int CONN>
+__device__ __forceinline__ void fq_relax(const SweepParams &p, bool valid, uint32_t e, uint32_t *next,
+                                         uint32_t *cnt, uint32_t *out, uint32_t *out_tail, int lane)
+{
+    constexpr int kN = CONN == 8 ? 8 : 4;
+    FqPixel q{0, 0, 0};
+    if (valid) q = fq_decode(p, e);
+    const ReconImage &d = p.b.img[q.img];
+    const int64_t o0 = (int64_t)q.row * d.Wp + q.col;
+    const uint32_t v = valid ? (uint32_t)__ldcg(d.Rw + o0) : 0u;
+    uint32_t iq[kN], rq[kN];
+    uint32_t inside = 0;   // bit k: neighbour k lies in the padded image
+#pragma unroll
+    for (int k = 0; k < kN; ++k) {
+        const int dr = k == 0 ? -1 : k == 1 ? 1 : k < 4 ? 0 : (k & 1 ? 1 : -1);
+        const int dc = k < 2 ? 0 : k == 2 ? -1 : k == 3 ? 1 : (k < 6 ? -1 : 1);
+        const int rr = q.row + dr, cc = q.col + dc;
+        iq[k] = rq[k] = 0u;
+        if (valid && rr >= 0 && rr < d.Hp && cc >= 0 && cc < d.Wp) {
+            const int64_t o = o0 + (int64_t)dr * d.Wp + dc;
+            iq[k] = __ldg(d.Iw + o);
+            rq[k] = __ldcg(d.Rw + o);
+            inside |= 1u << k;
+        }
+    }
+    uint32_t raised = 0;
+#pragma unroll
+    for (int k = 0; k < kN; ++k) {
+        const int dr = k == 0 ? -1 : k == 1 ? 1 : k < 4 ? 0 : (k & 1 ? 1 : -1);
+        const int dc = k < 2 ? 0 : k == 2 ? -1 : k == 3 ? 1 : (k < 6 ? -1 : 1);
+        const uint32_t nv = min(v, iq[k]);
+        if (((inside >> k) & 1u) && nv > rq[k] && fq_raise(d.Rw + o0 + (int64_t)dr * d.Wp + dc, nv))
+            raised |= 1u << k;
+    }
+#pragma unroll
+    for (int k = 0; k < kN; ++k) {
+        const int dr = k == 0 ? -1 : k == 1 ? 1 : k < 4 ? 0 : (k & 1 ? 1 : -1);
+        const int dc = k < 2 ? 0 : k == 2 ? -1 : k == 3 ? 1 : (k < 6 ? -1 : 1);
+        const int rr = q.row + dr, cc = q.col + dc;
+        const bool r_k = (raised >> k) & 1u;
+        const uint32_t eq = r_k ? fq_entry(d.tile_base + (cc / kTW) * d.tiles_y + rr / kTH, rr % kTH, cc % kTW) : 0u;
+        fq_push(p, r_k, eq, next, cnt, out, out_tail, lane);
+    }
+}
+
+// Grid barrier between the drain's rounds: bar[0] arrivals, bar[1]
+// generation. The wait ends when every CTA has arrived, or early once the
+// abort or the overflow word is set (both are sticky and stop every CTA at
+// its next check, so none waits for a CTA that has left) or the time bound
+// passes. Returns false when it ended early.
+__device__ __forceinline__ bool fq_barrier(const SweepParams &p, uint32_t *bar, uint64_t t0)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        const uint32_t gen = ld_acquire(bar + 1);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            uint32_t spins = 0;
+            while (ld_acquire(bar + 1) == gen) {
+                if (++spins > 64) __nanosleep(64);
+                if ((spins & 63u) == 0u) {
+                    if (ld_acquire(p.abort) || ld_acquire(p.fctl + kFqOver)) {
+                        s_ok = 0;
+                        break;
+                    }
+                    if (globaltimer_ns() - t0 > p.timeout_ns) {
+                        raise_status(p.err, RT_ETIMEOUT);
+                        atomicExch(p.abort, 1u);
+                        s_ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The drain. Round r: CTAs take chunks of the round's global queue into a
+// shared-memory queue and cascade locally (each step pops the whole local
+// queue, __syncthreads, the pushes become the next local queue) until the
+// chunk's cascade dies out, then take another chunk; pushes that overflow
+// the local queue go to the next round's global queue. A grid barrier ends
+// the round (the launch is cooperative, so every CTA is resident). The
+// abort word, the time bound, the visit bound (kFqPopsPerVisit pops count as
+// one tile visit, after the visits already spent) and the overflow word are
+// checked at every chunk and every 64 local steps.
+template <int CONN>
+__global__ void __launch_bounds__(kFqThreads) recon_frontier_kernel(SweepParams p)
+{
+    __shared__ uint32_t sq[2][kFqLocal];
+    __shared__ uint32_t s_cnt[3];
+    __shared__ uint32_t s_lo, s_hi, s_stop;
+    __shared__ uint32_t s_pops, s_told;   // pops of this CTA; the part added to the global count
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint32_t *ctl = p.fctl;
+    unsigned long long *pops_all = reinterpret_cast<unsigned long long *>(ctl + kFqPops);
+    const unsigned long long bound = (unsigned long long)p.max_visits * kFqPopsPerVisit;
+    const uint64_t t0 = globaltimer_ns();
+    if (tid == 0) s_pops = s_told = 0u;
+    bool go = ld_acquire(ctl + kFqOver) == 0u && ld_acquire(p.abort) == 0u;
+    for (int round = 0; go; ++round) {
+        const uint32_t *in = p.fq[round & 1];
+        uint32_t *out = p.fq[(round + 1) & 1];
+        uint32_t *out_tail = ctl + kFqTail + round + 1;
+        const uint32_t n_in = min(ld_acquire(ctl + kFqTail + round), p.fq_cap);
+        if (tid == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = 0u;
+        __syncthreads();
+        uint32_t n = 0, step = 0;
+        int cur = 0;
+        for (;;) {
+            if (n == 0u || (step & 63u) == 63u) {
+                if (tid == 0) {
+                    uint32_t stop = ld_acquire(p.abort) | ld_acquire(ctl + kFqOver);
+                    const uint32_t add = s_pops - s_told;
+                    s_told = s_pops;
+                    const unsigned long long done = add ? atomicAdd(pops_all, (unsigned long long)add) + add : 0ull;
+                    const bool spent = bound && (unsigned long long)ld_acquire(p.spent) * kFqPopsPerVisit + done > bound;
+                    if (!stop && (spent || globaltimer_ns() - t0 > p.timeout_ns)) {
+                        raise_status(p.err, RT_ETIMEOUT);
+                        atomicExch(p.abort, 1u);
+                        stop = 1u;
+                    }
+                    uint32_t lo = 0, hi = 0;
+                    if (!stop && n == 0u) {
+                        lo = atomicAdd(ctl + kFqHead + round, (uint32_t)kFqGrab);
+                        hi = min(lo + (uint32_t)kFqGrab, n_in);
+                    }
+                    s_lo = lo;
+                    s_hi = hi;
+                    s_stop = stop;
+                }
+                __syncthreads();
+                if (s_stop) break;
+                if (n == 0u) {
+                    const uint32_t lo = s_lo, hi = s_hi;
+                    if (lo >= hi) break;
+                    n = hi - lo;
+                    for (uint32_t i = tid; i < n; i += kFqThreads) sq[cur][i] = __ldcg(in + lo + i);
+                    __syncthreads();
+                }
+            }
+            // step s pushes into s_cnt[s % 3]; the counter of step s + 1 was
+            // last read at the start of step s - 1, before the barrier that
+            // began this step, so it can be cleared now
+            uint32_t *cnt = &s_cnt[step % 3u];
+            if (tid == 0) s_cnt[(step + 1u) % 3u] = 0u;
+            for (uint32_t base = (uint32_t)warp * 32u; base < n; base += kFqThreads) {
+                const uint32_t i = base + (uint32_t)lane;
+                const bool valid = i < n;
+                fq_relax<CONN>(p, valid, valid ? sq[cur][i] : 0u, sq[cur ^ 1], cnt, out, out_tail, lane);
+                if (lane == 0) atomicAdd(&s_pops, min(n - base, 32u));
+            }
+            __syncthreads();
+            n = min(*cnt, (uint32_t)kFqLocal);
+            cur ^= 1;
+            ++step;
+        }
+        if (!fq_barrier(p, ctl + kFqBar, t0)) break;
+        // the round's spill count is final here (the next round spills into
+        // the next counter), so every CTA takes the same decision; the abort
+        // and overflow words may be set later by a CTA already in the next
+        // round, which the early exits of its checks and barrier absorb
+        if (ld_acquire(p.abort) || ld_acquire(ctl + kFqOver)) break;
+        if (ld_acquire(out_tail) == 0u) break;
+        if (round + 2 >= kFqRounds) {   // the next round would have no spill counter
+            if (tid == 0) atomicExch(ctl + kFqOver, 1u);
+            break;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_pops && p.visits) atomicAdd(p.visits + 2, s_pops);
+    // Hand over to the directional sweeps: nothing to do (pending 0), or,
+    // after an overflow, every tile flagged for a dense visit with its edge
+    // columns refreshed from the drained image.
+    if (ld_acquire(p.abort)) return;
+    const bool over = ld_acquire(ctl + kFqOver) != 0u;
+    const int n = p.nvirt ? (int)*p.nvirt : p.ntiles;
+    if (over) {
+        for (int v = blockIdx.x * kFqThreads + tid; v < n; v += gridDim.x * kFqThreads) {
+            const int t = p.map ? p.map[v] : v;
+            const ReconImage &d = p.b.img[find_image(p, t)];
+            const int lt = t - d.tile_base;
+            const int tx = lt / d.tiles_y, ty = lt - tx * d.tiles_y;
+            const uint8_t *src = d.Rw + (int64_t)ty * kTH * d.Wp + tx * kTW;
+            uint8_t *ce = d.Cw + (int64_t)lt * kEdgeBytes;
+            for (int r = 0; r < kTH; ++r) {
+                ce[r] = __ldcg(src + (int64_t)r * d.Wp);
+                ce[kTH + r] = __ldcg(src + (int64_t)r * d.Wp + kTW - 1);
+            }
+            p.flags[t] = kDense;
+        }
+    }
+    if (blockIdx.x == 0 && tid == 0) *p.pending = over ? (uint32_t)n : 0u;
+}
+
+cudaError_t launch_recon_frontier(const SweepParams &p, int conn, int num_sms, cudaStream_t s, int *grid_used)
+{
+    const void *fn = conn == 8 ? (const void *)recon_frontier_kernel<8> : (const void *)recon_frontier_kernel<4>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFqThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = per_sm * num_sms;
+    if (grid > p.ntiles) grid = p.ntiles;   // small batches: fewer CTAs at the barriers
+    if (grid < 1) grid = 1;
+    if (grid_used) *grid_used = grid;
+    SweepParams pp = p;
+    void *args[] = {&pp};
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kFqThreads), args, 0, s);
 }
 
 // --------------------------------------------------------------- output

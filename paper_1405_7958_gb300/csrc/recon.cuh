@@ -47,8 +47,8 @@ struct ReconBatch {
 
 // Schedules the picker chooses between: entry c (c < kPickClasses) is class
 // c of the network, entry kPickClasses the plain schedule of the call (the
-// fall-back). group = variant - 1 (0 raster, 1 queue, 2 hybrid); max_local =
-// that schedule's sweep iterations per dense visit.
+// fall-back). group = variant - 1 (0 raster, 1 queue, 2 hybrid, 3 frontier);
+// max_local = that schedule's sweep iterations per dense visit.
 constexpr int kPickClasses = 3;
 constexpr int kPickEntries = kPickClasses + 1;
 struct PickTable {
@@ -72,7 +72,29 @@ struct SweepParams {
     const uint32_t *nvirt;    // with map: number of tiles the launch covers (device word)
     const int32_t *pick;      // NULL: max_local for every tile; else image i runs table.max_local of pick[i]
     PickTable table;
+    // RT_FRONTIER: the two global frontier queues (entries tile << 11 | row << 6
+    // | column, row and column within the 32 x 64 tile), their capacity in
+    // entries, and their control words (kFq* offsets)
+    uint32_t *fq[2];
+    uint32_t fq_cap;
+    uint32_t *fctl;
 };
+
+// Control words of the global frontier queues. Round r drains the queue
+// fq[r & 1] of fctl[kFqTail + r] entries (CTAs take them in chunks through
+// fctl[kFqHead + r]) and spills into fq[(r + 1) & 1]; a grid barrier
+// separates the rounds. Past kFqRounds rounds, or once an entry finds its
+// queue full, the overflow word is set and the directional sweeps finish
+// the propagation.
+constexpr int kFqRounds = 1024;
+constexpr int kFqTail = 0;
+constexpr int kFqHead = kFqRounds;
+constexpr int kFqBar = 2 * kFqRounds;
+constexpr int kFqOver = 2 * kFqRounds + 2;
+constexpr int kFqPops = 2 * kFqRounds + 4;         // 64-bit count of the drain's pops so far
+constexpr int kFqCtlWords = 2 * kFqRounds + 6;
+constexpr int kFqPopsPerVisit = kTH * kTW;          // pops counted as one tile visit against max_visits
+constexpr int64_t kFqMaxTiles = int64_t(1) << 21;   // tiles an entry can name
 
 // Control words of a propagation (device, zeroed before the init kernel):
 // kCtlPending: pending count of an ungrouped launch; kCtlVisits..+2: the
@@ -85,7 +107,7 @@ constexpr int kCtlGroupCount = 8;
 constexpr int kCtlSpent = 12;
 constexpr int kCtlAbort = 13;
 constexpr int kCtlWords = 16;
-constexpr int kGroups = 3;    // RT_RASTER, RT_QUEUE, RT_HYBRID
+constexpr int kGroups = 4;    // RT_RASTER, RT_QUEUE, RT_HYBRID, RT_FRONTIER
 
 void plan_recon_image(ReconImage &d, int H, int W);
 cudaError_t launch_marker(const uint8_t *mask, int64_t ld_mask, uint8_t *marker, int64_t ld_marker, int H,
@@ -93,7 +115,8 @@ cudaError_t launch_marker(const uint8_t *mask, int64_t ld_mask, uint8_t *marker,
 // pick == NULL: every tile starts with flag0, ctl[kCtlPending] counts them.
 // pick != NULL (device, one table entry per image; out-of-range entries are
 // the plain schedule): an image propagates in group table.group[entry];
-// tiles of raster and queue images start flagged, hybrid ones not;
+// tiles of raster and queue images start flagged, hybrid and frontier ones
+// not;
 // map[g * ntiles + k] lists the tiles of group g in batch order, with their
 // count and pending count in ctl.
 cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *ctl, uint32_t flag0,
@@ -101,6 +124,13 @@ cudaError_t launch_recon_init(const ReconBatch &b, uint32_t *flags, uint32_t *ct
                               cudaStream_t s);
 // one dense visit of every tile (non-persistent)
 cudaError_t launch_recon_dense(const SweepParams &p, int conn, cudaStream_t s);
+// RT_FRONTIER after the dense visits: every flagged tile (flag cleared) raises
+// the pixels its neighbours allow and appends them to fq[0]
+cudaError_t launch_recon_seed(const SweepParams &p, int conn, cudaStream_t s);
+// RT_FRONTIER: persistent CTAs drain the global frontier queues; then the
+// group's pending count is 0, or, after an overflow, every tile is flagged
+// for the directional sweeps that must follow (launch_recon_persistent)
+cudaError_t launch_recon_frontier(const SweepParams &p, int conn, int num_sms, cudaStream_t s, int *grid_used);
 // persistent visits of flagged tiles until quiescence; queue = 1: queue visits
 cudaError_t launch_recon_persistent(const SweepParams &p, int conn, int queue, int num_sms, cudaStream_t s,
                                     int *grid_used);

@@ -45,5 +45,5 @@ def test_table_tunes_once_per_class_and_persists(tmp_path, monkeypatch):
 
 def test_candidates_cover_both_schedules():
     vs = {v for v, _ in autotune.CANDIDATES}
-    assert vs == {autotune.rt.RT_RASTER, autotune.rt.RT_HYBRID}
+    assert vs == {autotune.rt.RT_RASTER, autotune.rt.RT_HYBRID, autotune.rt.RT_FRONTIER}
     assert all(m >= 0 for _, m in autotune.CANDIDATES)

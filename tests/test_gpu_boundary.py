@@ -30,11 +30,13 @@ def host(t):
     return t.cpu().numpy()
 
 
-@pytest.mark.parametrize("variant", ["RT_RASTER", "RT_QUEUE", "RT_HYBRID"])
+@pytest.mark.parametrize("variant", ["RT_RASTER", "RT_QUEUE", "RT_HYBRID", "RT_FRONTIER"])
 def test_visit_bound_runs_out_and_context_recovers(rt, variant):
     """A spiral corridor needs many visits of each of its 15 tiles; with one
     visit per tile allowed the propagation stops with RT_ETIMEOUT, below the
-    reconstruction (it only ever raises pixels towards it)."""
+    reconstruction (it only ever raises pixels towards it). RT_FRONTIER's
+    dense first pass spends the one visit per tile, and the drain's pops count
+    against the same bound (2048 pops per visit)."""
     I = synth.spiral(129, low=0)
     J = np.zeros_like(I)
     J[0, 0] = I[0, 0]
@@ -53,20 +55,23 @@ def test_visit_bound_runs_out_and_context_recovers(rt, variant):
     ctx.close()
 
 
-def test_time_bound_runs_out_and_context_recovers(rt):
+@pytest.mark.parametrize("variant", ["RT_RASTER", "RT_FRONTIER"])
+def test_time_bound_runs_out_and_context_recovers(rt, variant):
     """A 768 x 768 spiral's front crosses thousands of tile edges one after
-    another (each ring of the corridor crosses every tile on its way); 2 ms
-    of device time is not enough."""
+    another (each ring of the corridor crosses every tile on its way), and a
+    pixel frontier follows its 300,000-pixel corridor one step at a time; 2 ms
+    of device time is not enough for either."""
     I = synth.spiral(768, low=0)
     J = np.zeros_like(I)
     J[0, 0] = I[0, 0]
     ctx = rt.Context()
+    v = getattr(rt, variant)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     ctx.set_limits(timeout_ms=2)
-    rt.reconstruct(dev(I), dev(J), conn=8, status=st, ctx=ctx)
+    rt.reconstruct(dev(I), dev(J), conn=8, variant=v, status=st, ctx=ctx)
     assert int(host(st)[0]) == rt.RT_ETIMEOUT
     ctx.set_limits(0, 0)
-    got = host(rt.reconstruct(dev(I), dev(J), conn=8, status=st, ctx=ctx))
+    got = host(rt.reconstruct(dev(I), dev(J), conn=8, variant=v, status=st, ctx=ctx))
     assert int(st.item()) == rt.RT_OK
     assert np.array_equal(got, oracle.recon(J, I, 8))
     ctx.close()
@@ -116,6 +121,31 @@ def test_batch_of_40_uneven_tiles_eager_and_graph(rt):
     torch.cuda.synchronize()
     for o, w in zip(outs, want):
         assert int(host(o["n_kept"])[0]) == w["n_kept"]
+        for k in ("R", "F", "L", "D"):
+            assert np.array_equal(host(o[k]), w[k])
+    ctx.close()
+
+
+@pytest.mark.parametrize("cap", [0, 500])
+def test_batch_frontier_variant(rt, cap):
+    """rt_segment_batch with RT_FRONTIER for every tile (one seeding and one
+    drain over the whole chunk, entries naming tiles of several images), with
+    the default queues and with queues small enough to overflow: every
+    output is the oracle's, and the size query counts the queues."""
+    shapes = [(300, 500), (640, 256), (1024, 1024), (77, 1300), (513, 700)]
+    imgs = [synth.tile(H, W, 60 + i, 1 + H * W // 4000, background="flat" if i % 2 else "perlin")
+            for i, (H, W) in enumerate(shapes)]
+    want = [oracle.chain(x) for x in imgs]
+    ctx = rt.Context()
+    ctx.set_queue_capacity(cap)
+    p = rt.SegParams(variant=rt.RT_FRONTIER)
+    need = rt.segment_workspace_bytes(shapes, p, ctx=ctx)
+    assert need > rt.segment_workspace_bytes(shapes, rt.SegParams())
+    outs = rt.segment_batch([dev(x) for x in imgs], p, ctx=ctx)
+    torch.cuda.synchronize()
+    assert ctx.workspace_bytes() >= need
+    for o, w in zip(outs, want):
+        assert int(host(o["status"])[0]) == 0
         for k in ("R", "F", "L", "D"):
             assert np.array_equal(host(o[k]), w[k])
     ctx.close()

@@ -139,9 +139,10 @@ def test_training_reduces_loss(rt):
 
 
 VARIANT_CLASSES = ((1, 12), (2, 0), (3, 0))    # RT_RASTER, RT_QUEUE, RT_HYBRID as the three classes
+FRONTIER_CLASSES = ((1, 12), (4, 0), (3, 0))   # RT_RASTER, RT_FRONTIER, RT_HYBRID
 
 
-@pytest.mark.parametrize("classes", [None, VARIANT_CLASSES], ids=["budgets", "variants"])
+@pytest.mark.parametrize("classes", [None, VARIANT_CLASSES, FRONTIER_CLASSES], ids=["budgets", "variants", "frontier"])
 def test_learned_policy_same_bytes_as_plain(rt, classes):
     """Every class of the picker, forced (the default visit budgets, and a
     table of the three variants): the oracle's bytes; a confidence threshold
@@ -207,15 +208,17 @@ def test_learned_policy_mixed_variants_in_one_batch(rt):
     ctx.close()
 
 
-def test_learned_policy_in_cuda_graph(rt):
+@pytest.mark.parametrize("classes", [VARIANT_CLASSES, FRONTIER_CLASSES], ids=["variants", "frontier"])
+def test_learned_policy_in_cuda_graph(rt, classes):
     """The learned path has no host round trip, so it captures into a CUDA
-    graph; replays give the oracle's bytes and the same picks."""
+    graph (the frontier class included: its queue counters are reset by a
+    memset node); replays give the oracle's bytes and the same picks."""
     shapes = [(300, 500), (700, 640), (1100, 333)]
     imgs = [synth.config2_tile(80 + i, H=H, W=W) for i, (H, W) in enumerate(shapes)]
     d = [torch.from_numpy(x).cuda() for x in imgs]
     pk = _height_picker(rt)
     ctx = rt.Context()
-    rt.set_picker_classes(VARIANT_CLASSES, ctx)
+    rt.set_picker_classes(classes, ctx)
     pk.attach(ctx)
     s = torch.cuda.Stream()
     p = rt.SegParams(policy=1)

@@ -56,7 +56,7 @@ def test_recon_config1(rt):
     assert np.array_equal(host(rt.reconstruct(dev(I), J, conn=8)), want)
 
 
-VARIANTS = ["RT_RASTER", "RT_QUEUE", "RT_HYBRID"]
+VARIANTS = ["RT_RASTER", "RT_QUEUE", "RT_HYBRID", "RT_FRONTIER"]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -112,6 +112,41 @@ def test_recon_full_4k_tile(rt, variant):
     want = oracle.recon(oracle.marker(I, 30), I, 8)
     got = host(rt.reconstruct(dev(I), None, h_offset=30, conn=8, variant=getattr(rt, variant)))
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_frontier_queue_overflow_hands_over_to_the_sweeps(rt, conn):
+    """RT_FRONTIER with global queues too small for the seeds or for the
+    drain's spills: the directional sweeps finish the propagation from the
+    drained state, and the bytes are the oracle's. Capacity 0 restores the
+    default (one entry per padded pixel)."""
+    ctx = rt.Context()
+    cases = [synth.config2_tile(11, H=700, W=900), synth.spiral(129, low=0),
+             synth.tile(640, 832, 5, 60, background="flat")]
+    for I in cases:
+        J = oracle.marker(I, 30)
+        want = oracle.recon(J, I, conn)
+        for cap in (1, 64, 3000, 0):
+            ctx.set_queue_capacity(cap)
+            st = torch.zeros(1, dtype=torch.int32, device="cuda")
+            got = host(rt.reconstruct(dev(I), dev(J), conn=conn, variant=rt.RT_FRONTIER, status=st, ctx=ctx))
+            assert np.array_equal(got, want), (I.shape, cap)
+            assert int(st.item()) == rt.RT_OK
+    ctx.close()
+
+
+def test_frontier_pops_follow_the_front(rt):
+    """On a flat-background tile the dense first pass leaves a thin front:
+    the frontier drain pops pixels (counted in the statistics), and the
+    output is the oracle's."""
+    ctx = rt.Context()
+    I = synth.tile(1024, 1024, 3, 200, background="flat")
+    want = oracle.recon(oracle.marker(I, 30), I, 8)
+    got = host(rt.reconstruct(dev(I), None, h_offset=30, conn=8, variant=rt.RT_FRONTIER, ctx=ctx))
+    assert np.array_equal(got, want)
+    visits, iters, pops = ctx.recon_stats()
+    assert pops > 0 and visits >= (1024 // 32) * (1024 // 64)
+    ctx.close()
 
 
 # ---------------------------------------------------------------- fill holes
