@@ -362,10 +362,14 @@ class Pipeline:
 
 
 def copy_rates(dev, nbytes=1 << 30):
-    """Plain pinned host <-> device copy rates (GB/s, best of 3) on this machine."""
+    """Plain pinned host <-> device copy rates (GB/s, best of 3) on this machine:
+    each direction alone, and both directions at once (two streams), which
+    share the host link."""
     import torch
     h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h2 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
     d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     out = {}
     for name, (dst, src) in (("h2d_gbs", (d, h)), ("d2h_gbs", (h, d))):
         best = 0.0
@@ -377,7 +381,24 @@ def copy_rates(dev, nbytes=1 << 30):
             e1.synchronize()
             best = max(best, nbytes / (e0.elapsed_time(e1) / 1000) / 1e9)
         out[name] = round(best, 1)
-    del h, d
+    sa, sb = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    both = {"h2d_concurrent_gbs": 0.0, "d2h_concurrent_gbs": 0.0}
+    for _ in range(3):
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(sa):
+            ev[0].record(sa)
+            d.copy_(h, non_blocking=True)
+            ev[1].record(sa)
+        with torch.cuda.stream(sb):
+            ev[2].record(sb)
+            h2.copy_(d2, non_blocking=True)
+            ev[3].record(sb)
+        torch.cuda.synchronize()
+        both["h2d_concurrent_gbs"] = max(both["h2d_concurrent_gbs"], nbytes / (ev[0].elapsed_time(ev[1]) / 1000) / 1e9)
+        both["d2h_concurrent_gbs"] = max(both["d2h_concurrent_gbs"], nbytes / (ev[2].elapsed_time(ev[3]) / 1000) / 1e9)
+    out.update({k: round(v, 1) for k, v in both.items()})
+    del h, h2, d, d2
     return out
 
 
@@ -644,32 +665,48 @@ def run_native(a, rank, world, local_rank):
     # end to end through the public API with host buffers: every step copies
     # its inputs from pinned host memory, runs the chain and copies labels and
     # distances back. Steps alternate between the compute streams (one context
-    # each); the read-backs run on a stream of their own, from output sets
-    # rotated over twice as many steps, so no compute stream waits behind the
-    # read-back queue
+    # each). The input copies run on a stream of their own two steps ahead,
+    # the read-backs on another, into and from input and output sets rotated
+    # over twice as many steps as there are compute streams, so no compute
+    # stream waits behind a copy queue
     e2e = None
     if not a.no_e2e:
         nset = 2 * nst
+        ahead = 2
         h_in = [im.cpu().pin_memory() for im in imgs]
         h_L = [[torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in imgs] for _ in range(nset)]
         h_D = [[torch.empty((a.size, a.size), dtype=torch.int32).pin_memory() for _ in imgs] for _ in range(nset)]
-        d_in = [[torch.empty_like(x, device=dev) for x in imgs] for _ in range(nst)]
+        d_in = [[torch.empty_like(x, device=dev) for x in imgs] for _ in range(nset)]
         read_s = torch.cuda.Stream(device=dev)
+        in_s = torch.cuda.Stream(device=dev)
         outs_e = [None] * nset
         read_done = [None] * nset
+        used = [None] * nset     # the set's last compute, after which its inputs may be overwritten
+        in_ready = [None] * nset
+        n_steps = [0]            # steps to run: no inputs are loaded past the last one
+
+        def e2e_load(k):
+            b = k % nset
+            with torch.cuda.stream(in_s):
+                if used[b] is not None:
+                    in_s.wait_event(used[b])
+                for h, d in zip(h_in, d_in[b]):
+                    d.copy_(h, non_blocking=True)
+                in_ready[b] = torch.cuda.Event()
+                in_ready[b].record(in_s)
 
         def e2e_step(k):
             j, b = k % nst, k % nset
             s = pipe.streams[j]
             with torch.cuda.stream(s):
+                s.wait_event(in_ready[b])
                 if read_done[b] is not None:
                     s.wait_event(read_done[b])      # the set's previous read-back has finished
-                for h, d in zip(h_in, d_in[j]):
-                    d.copy_(h, non_blocking=True)
-                outs_e[b] = rt.segment_batch(d_in[j], learned, outputs=outs_e[b], ctx=pipe.ctxs[j], stream=s,
+                outs_e[b] = rt.segment_batch(d_in[b], learned, outputs=outs_e[b], ctx=pipe.ctxs[j], stream=s,
                                              want_recon=False, want_filled=False)
                 computed = torch.cuda.Event()
                 computed.record(s)
+                used[b] = computed
             read_s.wait_event(computed)
             with torch.cuda.stream(read_s):
                 for o, hl, hd in zip(outs_e[b], h_L[b], h_D[b]):
@@ -677,18 +714,28 @@ def run_native(a, rank, world, local_rank):
                     hd.copy_(o["D"], non_blocking=True)
                 read_done[b] = torch.cuda.Event()
                 read_done[b].record(read_s)
+            if k + ahead < n_steps[0]:
+                e2e_load(k + ahead)
 
-        for k in range(max(nset, a.warmup)):
+        nwarm = max(nset, a.warmup)
+        n_steps[0] = nwarm              # warm-up: inputs of warm-up steps only
+        for k in range(ahead):
+            e2e_load(k)
+        for k in range(nwarm):
             e2e_step(k)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(pipe.streams[0])
-        for s in pipe.streams[1:] + [read_s]:
+        for s in pipe.streams[1:] + [read_s, in_s]:
             s.wait_event(e0)
-        for k in range(a.steps):
+        # timed: every step's input copy is inside the region
+        n_steps[0] = nwarm + a.steps
+        for k in range(nwarm, nwarm + ahead):
+            e2e_load(k)
+        for k in range(nwarm, nwarm + a.steps):
             e2e_step(k)
-        for s in pipe.streams[1:] + [read_s]:
+        for s in pipe.streams[1:] + [read_s, in_s]:
             ev = torch.cuda.Event()
             ev.record(s)
             pipe.streams[0].wait_event(ev)
@@ -704,8 +751,10 @@ def run_native(a, rank, world, local_rank):
         h2d, d2h = a.batch * px, a.batch * px * 8
         e2e = {"value": world * a.batch * a.steps / (float(tt.item()) / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "streams": nst, "output_sets": nset, "copy_gbs": rates,
-               "copy_bound_tiles_s": a.batch / max(h2d / (rates["h2d_gbs"] * 1e9), d2h / (rates["d2h_gbs"] * 1e9))}
+               "streams": nst, "output_sets": nset, "input_lookahead_steps": ahead, "copy_gbs": rates,
+               "copy_bound_tiles_s": a.batch / max(h2d / (rates["h2d_gbs"] * 1e9), d2h / (rates["d2h_gbs"] * 1e9)),
+               "copy_bound_concurrent_tiles_s": a.batch / max(h2d / (rates["h2d_concurrent_gbs"] * 1e9),
+                                                              d2h / (rates["d2h_concurrent_gbs"] * 1e9))}
         del h_in, h_L, h_D, d_in
 
     cpu = None

@@ -33,7 +33,8 @@ struct rt_ctx {
     bool timing = false;
     const uint16_t *picker_wb = nullptr;   // attached picker (caller-owned device memory)
     const float *picker_norm = nullptr;
-    int32_t *picks_host = nullptr;         // pinned: picker classes of the last learned chunk
+    int32_t *picks_host = nullptr;         // pinned, mapped: picker classes of the last learned chunk
+    int32_t *picks_mapped = nullptr;       // the same memory as the device sees it
     cudaEvent_t picks_ev = nullptr;        // recorded after their copy (not under stream capture)
     bool picks_ev_valid = false;
     int n_last_picks = 0;
@@ -152,6 +153,19 @@ rt_status cuda_status(cudaError_t e)
     return RT_ECUDA;
 }
 
+// Zeroes n words of device memory. The chain clears its control words with
+// this kernel rather than cudaMemsetAsync, so that nothing in it can wait
+// behind the caller's copies on a copy engine.
+__global__ void zero_words_kernel(uint32_t *p, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0u;
+}
+cudaError_t zero_words(void *p, int n, cudaStream_t s)
+{
+    zero_words_kernel<<<(n + 255) / 256 < 16 ? (n + 255) / 256 : 16, 256, 0, s>>>(static_cast<uint32_t *>(p), n);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- recon
 struct ReconWs {
     uint32_t *flags;   // per tile
@@ -250,7 +264,8 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
     // queue visit then seeds every pixel); RT_HYBRID / RT_FRONTIER: nothing
     // flagged, the dense pass over all tiles flags what remains.
     const uint32_t flag0 = variant == RT_HYBRID || variant == RT_FRONTIER ? 0u : 2u;
-    RT_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, kCtlWords * sizeof(uint32_t), s));
+    RT_CUDA_TRY(zero_words(w.ctl, kCtlWords, s));
+    ctx->launches += 1;
     {
         Phase ph(ctx, RT_PHASE_RECON_INIT, s);
         RT_CUDA_TRY(launch_recon_init(b, w.flags, w.ctl, flag0, pick, table, w.map, err, s));
@@ -299,7 +314,8 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
             // seed and drain the global frontier queues; the directional
             // sweeps that follow find nothing flagged unless a queue
             // overflowed
-            RT_CUDA_TRY(cudaMemsetAsync(w.fctl, 0, kFqCtlWords * sizeof(uint32_t), s));
+            RT_CUDA_TRY(zero_words(w.fctl, kFqCtlWords, s));
+            ctx->launches += 1;
             RT_CUDA_TRY(launch_recon_seed(p, conn, s));
             RT_CUDA_TRY(launch_recon_frontier(p, conn, ctx->num_sms, s, &grid));
             ctx->launches += 2;
@@ -337,6 +353,13 @@ struct StatusOut {
 __global__ void copy_status_kernel(const int32_t *src, StatusOut o, int n)
 {
     if ((int)threadIdx.x < n && o.dst[threadIdx.x]) *o.dst[threadIdx.x] = *src;
+}
+
+// the picker's classes of a chunk into the caller-visible pinned buffer
+__global__ void copy_picks_kernel(const int32_t *src, int32_t *dst, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    __threadfence_system();
 }
 
 bool bad_params(const rt_seg_params &P)
@@ -501,7 +524,8 @@ rt_status rt_create(rt_ctx **ctx, int device, size_t workspace_bytes)
     c->device = device;
     DeviceGuard g(device);
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaHostAlloc((void **)&c->picks_host, kMaxImgs * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->picks_host, kMaxImgs * sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->picks_mapped, c->picks_host, 0) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->picks_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (c->picks_host) cudaFreeHost(c->picks_host);
@@ -1019,7 +1043,8 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         Carve cv;
         cv.base = (char *)ctx->ws;
         layout_chunk(cv, c, tiles, c0, cn, P, learned, ctx);
-        RT_CUDA_TRY(cudaMemsetAsync(c.w.err, 0, sizeof(int32_t), s));
+        RT_CUDA_TRY(zero_words(c.w.err, 1, s));
+        ctx->launches += 1;
         if (!learned) {
             st = run_recon(ctx, c.b, c.w, P.conn_recon, P.variant, P.max_local, c.w.err, s, lim);
             if (st != RT_OK) return st;
@@ -1035,7 +1060,12 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
             }
             st = run_recon(ctx, c.b, c.w, P.conn_recon, P.variant, P.max_local, c.w.err, s, lim, c.picks);
             if (st != RT_OK) return st;
-            RT_CUDA_TRY(cudaMemcpyAsync(ctx->picks_host, c.picks, sizeof(int32_t) * cn, cudaMemcpyDeviceToHost, s));
+            // written by a kernel into the mapped pinned buffer: a copy-engine
+            // transfer here would queue behind the caller's read-backs on the
+            // same engine and hold up the rest of the chain
+            copy_picks_kernel<<<1, 32, 0, s>>>(c.picks, ctx->picks_mapped, cn);
+            RT_CUDA_TRY(cudaGetLastError());
+            ctx->launches += 1;
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusActive;
             if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cudaGetLastError();
             ctx->picks_ev_valid = cap == cudaStreamCaptureStatusNone;
