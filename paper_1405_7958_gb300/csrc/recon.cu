@@ -211,12 +211,16 @@ __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b)
 __device__ __forceinline__ uint32_t widen2(uint32_t v) { return __byte_perm(v, 0u, 0x4140); }
 __device__ __forceinline__ uint32_t narrow2(uint32_t w) { return __byte_perm(w, 0u, 0x4420); }
 
-// Flag bits of a tile: its halo changed, or it needs a dense visit.
-constexpr uint32_t kHalo = 1u, kDense = 2u;
+// Flag bits of a tile: it needs a dense visit (kDense), or one side of its
+// halo changed: the row above it (read by the down sweep, kTopHalo), the row
+// below it (read by the up sweep, kBotHalo), or a side column or corner
+// (read by the row pass, kSideHalo). kHalo: any of the three.
+constexpr uint32_t kTopHalo = 1u, kDense = 2u, kBotHalo = 4u, kSideHalo = 8u;
+constexpr uint32_t kHalo = kTopHalo | kBotHalo | kSideHalo;
 
 // Sets a tile's flag; returns 1 if the tile was already flagged (its visit
 // was counted before).
-__device__ __forceinline__ uint32_t mark_tile(uint32_t *flags, int t, uint32_t bits = kHalo)
+__device__ __forceinline__ uint32_t mark_tile(uint32_t *flags, int t, uint32_t bits)
 {
     return atomicOr(flags + t, bits) != 0u ? 1u : 0u;
 }
@@ -250,7 +254,7 @@ __device__ __forceinline__ void mark_neighbours(const SweepParams &p, const Reco
     uint32_t stale = 0;
 #pragma unroll
     for (int k = 0; k < 9; ++k)
-        if (c[k]) stale += mark_tile(p.flags, u[k], k == 0 ? self_bits : kHalo);
+        if (c[k]) stale += mark_tile(p.flags, u[k], k == 0 ? self_bits : k == 1 ? kBotHalo : k == 2 ? kTopHalo : kSideHalo);
     if (stale) atomicSub(p.pending, stale);
 }
 
@@ -297,7 +301,7 @@ struct WarpBuf {
 
 // One visit of tile t by a warp. Returns after marking the tiles to visit.
 template <int CONN>
-__device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, const WarpBuf &wb, int lane)
+__device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, uint32_t bits, const WarpBuf &wb, int lane)
 {
     const int img = find_image(p, t);
     const ReconImage &d = p.b.img[img];
@@ -329,57 +333,63 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
     }
     __syncwarp();
 
-    // Passes run in the cycle down, up, rows. Each pass is idempotent, so the
-    // tile is at a fixed point as soon as the two passes after the last one
-    // that changed something changed nothing.
-    bool converged = false;
+    // Passes run in the cycle down, up, rows; each pass is idempotent. `need`
+    // holds the pass kinds (1 down, 2 up, 4 rows) that must still run without
+    // a change: a pass that changes something requires the other two again, a
+    // clean one drops itself, and the tile is at its fixed point when none is
+    // left. A dense visit needs all three. A tile flagged only because part of
+    // its halo moved was at the fixed point for its old halo (a visit that
+    // stops short flags its own tile dense), so only the passes that read the
+    // moved part can change it: the visit starts with the first of those.
+    uint32_t need = (bits & kDense) || !(bits & kHalo)
+                        ? 7u
+                        : ((bits & kTopHalo) ? 1u : 0u) | ((bits & kBotHalo) ? 2u : 0u) | ((bits & kSideHalo) ? 4u : 0u);
+    const int start = (need & 1u) ? 0 : (need & 2u) ? 1 : 2;
     int it = 0;
-    int clean = 0;          // consecutive passes without a change
-    for (; it < max_local && !converged; ++it) {
+    for (; it < max_local && need; ++it) {
         bool ch = false;
-        // down sweep
-        uint32_t prev = topw;
+        uint32_t prev;
+        if (it > 0 || start == 0) {
+            // down sweep
+            prev = topw;
 #pragma unroll
-        for (int r = 0; r < kTH; ++r) {
-            uint32_t m = vmax2(R[r], prev);
-            if (CONN == 8) {
-                // lanes 0 and 31 get their own word back from the shuffles:
-                // the extra terms are in-tile neighbours anyway; the halo
-                // columns enter through the row pass
-                const uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
-                const uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
-                m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
+            for (int r = 0; r < kTH; ++r) {
+                uint32_t m = vmax2(R[r], prev);
+                if (CONN == 8) {
+                    // lanes 0 and 31 get their own word back from the shuffles:
+                    // the extra terms are in-tile neighbours anyway; the halo
+                    // columns enter through the row pass
+                    const uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
+                    const uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
+                    m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
+                }
+                const uint32_t nv = vmin2(m, Is[r * kTS]);
+                ch |= nv != R[r];
+                R[r] = nv;
+                prev = nv;
             }
-            const uint32_t nv = vmin2(m, Is[r * kTS]);
-            ch |= nv != R[r];
-            R[r] = nv;
-            prev = nv;
+            need = __any_sync(0xffffffffu, ch) ? 6u : need & ~1u;
+            if (!need) break;
         }
-        clean = __any_sync(0xffffffffu, ch) ? 0 : clean + 1;
-        if (clean >= 2) {
-            converged = true;
-            break;
-        }
-        ch = false;
-        // up sweep
-        prev = botw;
+        if (it > 0 || start <= 1) {
+            ch = false;
+            // up sweep
+            prev = botw;
 #pragma unroll
-        for (int r = kTH - 1; r >= 0; --r) {
-            uint32_t m = vmax2(R[r], prev);
-            if (CONN == 8) {
-                const uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
-                const uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
-                m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
+            for (int r = kTH - 1; r >= 0; --r) {
+                uint32_t m = vmax2(R[r], prev);
+                if (CONN == 8) {
+                    const uint32_t sl = __shfl_up_sync(0xffffffffu, prev, 1);
+                    const uint32_t sr = __shfl_down_sync(0xffffffffu, prev, 1);
+                    m = vmax2(m, vmax2(__byte_perm(sl, prev, 0x5432), __byte_perm(prev, sr, 0x5432)));
+                }
+                const uint32_t nv = vmin2(m, Is[r * kTS]);
+                ch |= nv != R[r];
+                R[r] = nv;
+                prev = nv;
             }
-            const uint32_t nv = vmin2(m, Is[r * kTS]);
-            ch |= nv != R[r];
-            R[r] = nv;
-            prev = nv;
-        }
-        clean = __any_sync(0xffffffffu, ch) ? 0 : clean + 1;
-        if (clean >= 2 && it > 0) {
-            converged = true;
-            break;
+            need = __any_sync(0xffffffffu, ch) ? 5u : need & ~2u;
+            if (!need) break;
         }
         ch = false;
         // left-to-right and right-to-left along every row (lane = row)
@@ -427,9 +437,9 @@ __device__ __forceinline__ uint32_t visit_tile(const SweepParams &p, int t, cons
 #pragma unroll
         for (int r = 0; r < kTH; ++r) R[r] = wb.sRT[r * kTS + lane];
         __syncwarp();
-        clean = __any_sync(0xffffffffu, ch) ? 0 : clean + 1;
-        if (clean >= 2) converged = true;
+        need = __any_sync(0xffffffffu, ch) ? 3u : need & ~4u;
     }
+    const bool converged = need == 0;
 
     // write back, and find which borders moved
     uint16_t *Rs = reinterpret_cast<uint16_t *>(d.Rw + (int64_t)r0 * Wp + c0) + lane;
@@ -640,7 +650,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_dense_kernel(SweepPar
     wb.sHL = wb.sIT + kTH * kTS;
     wb.sHR = wb.sHL + (kTH + 2);
     wb.sR0 = reinterpret_cast<uint16_t *>(wb.sHR + (kTH + 2));
-    const uint32_t it = visit_tile<CONN>(p, t, wb, lane);
+    const uint32_t it = visit_tile<CONN>(p, t, kDense, wb, lane);
     if (lane == 0 && p.max_visits) atomicAdd(p.spent, 1u);   // one visit per tile: within any bound
     if (lane == 0 && p.visits) {
         atomicAdd(p.visits, 1u);
@@ -721,7 +731,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
                 if (!got) continue;
                 __threadfence();
                 if (QUEUE) work += visit_queue<CONN>(p, t, got, qb, lane);
-                else work += visit_tile<CONN>(p, t, wb, lane);
+                else work += visit_tile<CONN>(p, t, got, wb, lane);
                 if (lane == 0) atomicSub(p.pending, 1u);
                 did = true;
                 ++nvisits;
