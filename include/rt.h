@@ -403,8 +403,11 @@ RT_API rt_status rt_set_picker(rt_ctx *ctx, const uint16_t *wb, const float *nor
 RT_API rt_status rt_set_picker_classes(rt_ctx *ctx, const int *variants, const int *max_locals);
 
 /* Classes the picker chose for the tiles of the last chunk (up to 32 tiles)
- * of the last learned rt_segment_batch call: 0..2, or 3 where the pick fell
- * back to the call's plain schedule (confidence below pick_min_prob). Copies
+ * of the last learned rt_segment_batch call: 0..2, or 3 where the tile ran
+ * the call's plain schedule: the pick fell back (confidence below
+ * pick_min_prob), or the picker was not run because no pick could change
+ * the schedule (a chunk of several tiles, where raster classes run at the
+ * plain budget, with a raster plain schedule and raster classes only). Copies
  * up to cap of them into classes (nullable) and returns how many there
  * were. The choices stay on the device during the call (the propagation
  * reads them there) and are copied to pinned host memory at its end; this
@@ -443,7 +446,9 @@ typedef struct {
     int policy;      /* RT_POLICY_PLAIN: `variant` and `max_local` for every tile;
                         RT_POLICY_LEARNED: the attached picker chooses a schedule per tile
                         (rt_set_picker_classes), and the plain schedule is kept whenever no
-                        picker is attached */
+                        picker is attached. In a chunk of several tiles a raster class runs
+                        at the plain budget (`max_local`): there the tiles share one launch,
+                        whose throughput, not a tile's latency, sets the time */
     int max_iters;   /* tile visits per 32 x 64 tile allowed to the propagation, as in
                         rt_set_limits; 0 = the context's bound */
     int timeout_ms;  /* device-time bound of each propagation; 0 = the context's (20 s) */

@@ -234,6 +234,21 @@ Limits ctx_limits(const rt_ctx *ctx) { return {ctx->max_iters, ctx->timeout_ns ?
 
 int default_max_local(int variant) { return variant == RT_HYBRID || variant == RT_FRONTIER ? 64 : 12; }
 
+// sweep budget of every raster tile in a launch shared by several tiles
+int shared_raster_budget(int max_local) { return max_local > 0 ? max_local : default_max_local(RT_RASTER); }
+
+// In a launch shared by several tiles every raster class runs at the plain
+// budget, so when the plain schedule and every class of the picker are
+// raster, no pick can change a tile's schedule and the picker is not run.
+bool picks_matter(const rt_ctx *ctx, const rt_seg_params &P, int n_tiles)
+{
+    if (n_tiles == 1) return true;
+    if (P.variant != RT_AUTO && P.variant != RT_RASTER) return true;
+    for (int c = 0; c < kPickClasses; ++c)
+        if (ctx->classes.group[c] != 0) return true;
+    return false;
+}
+
 rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int variant, int max_local, int32_t *err,
                     cudaStream_t s, Limits lim, const int32_t *pick = nullptr)
 {
@@ -252,14 +267,13 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
     if (variant == RT_FRONTIER && !fq_ok) variant = RT_HYBRID;
     // The picker learned its budgets on lone tiles, where a tile's latency
     // sets the time and short visits can win. Tiles that share a launch with
-    // others are bound by its throughput instead, and there budgets below
-    // the plain one only add visits (measured on uneven and 4K batches):
-    // they are raised to the plain budget.
-    if (pick && b.n > 1) {
-        const int plain_raster = max_local > 0 ? max_local : default_max_local(RT_RASTER);
+    // others are bound by its throughput instead: there a budget below the
+    // plain one only adds visits, and one above it adds visits too once
+    // revisits start at the moved side of the halo (measured on uneven and
+    // 4K batches). Raster classes run at the plain budget in shared launches.
+    if (pick && b.n > 1)
         for (int c = 0; c < kPickClasses; ++c)
-            if (table.group[c] == 0 && table.max_local[c] < plain_raster) table.max_local[c] = plain_raster;
-    }
+            if (table.group[c] == 0) table.max_local[c] = shared_raster_budget(max_local);
     // RT_RASTER / RT_QUEUE: every tile starts flagged for a dense visit (the
     // queue visit then seeds every pixel); RT_HYBRID / RT_FRONTIER: nothing
     // flagged, the dense pass over all tiles flags what remains.
@@ -356,9 +370,10 @@ __global__ void copy_status_kernel(const int32_t *src, StatusOut o, int n)
 }
 
 // the picker's classes of a chunk into the caller-visible pinned buffer
+// src NULL: every tile ran the plain schedule (class kPickClasses)
 __global__ void copy_picks_kernel(const int32_t *src, int32_t *dst, int n)
 {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src ? src[i] : kPickClasses;
     __threadfence_system();
 }
 
@@ -1051,19 +1066,21 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
         } else {
             // the picker chooses a variant per tile on the device; the
             // propagation reads its choices directly (no host round trip)
-            {
+            const bool pick = picks_matter(ctx, P, cn);
+            if (pick) {
                 Phase ph(ctx, RT_PHASE_PICK, s);
                 RT_CUDA_TRY(launch_features(c.fb, c.feat, s));
                 RT_CUDA_TRY(launch_mlp_forward(ctx->picker_wb, ctx->picker_norm, c.feat, cn, nullptr, nullptr, c.picks,
                                                (float)P.pick_min_prob / 1000.0f, kPickClasses, s));
                 ctx->launches += 5;
             }
-            st = run_recon(ctx, c.b, c.w, P.conn_recon, P.variant, P.max_local, c.w.err, s, lim, c.picks);
+            st = run_recon(ctx, c.b, c.w, P.conn_recon, P.variant, P.max_local, c.w.err, s, lim,
+                           pick ? c.picks : nullptr);
             if (st != RT_OK) return st;
             // written by a kernel into the mapped pinned buffer: a copy-engine
             // transfer here would queue behind the caller's read-backs on the
             // same engine and hold up the rest of the chain
-            copy_picks_kernel<<<1, 32, 0, s>>>(c.picks, ctx->picks_mapped, cn);
+            copy_picks_kernel<<<1, 32, 0, s>>>(pick ? c.picks : nullptr, ctx->picks_mapped, cn);
             RT_CUDA_TRY(cudaGetLastError());
             ctx->launches += 1;
             cudaStreamCaptureStatus cap = cudaStreamCaptureStatusActive;
