@@ -217,12 +217,16 @@ __device__ __forceinline__ uint32_t narrow2(uint32_t w) { return __byte_perm(w, 
 // (read by the row pass, kSideHalo). kHalo: any of the three.
 constexpr uint32_t kTopHalo = 1u, kDense = 2u, kBotHalo = 4u, kSideHalo = 8u;
 constexpr uint32_t kHalo = kTopHalo | kBotHalo | kSideHalo;
+// Set while a warp visits the tile: no other warp may take it then, since
+// two visits of one tile at once would write its pixels from different
+// states. Flag bits set meanwhile stay for a later visit.
+constexpr uint32_t kBusy = 0x80000000u;
 
 // Sets a tile's flag; returns 1 if the tile was already flagged (its visit
 // was counted before).
 __device__ __forceinline__ uint32_t mark_tile(uint32_t *flags, int t, uint32_t bits)
 {
-    return atomicOr(flags + t, bits) != 0u ? 1u : 0u;
+    return (atomicOr(flags + t, bits) & ~kBusy) != 0u ? 1u : 0u;
 }
 
 // Flags the neighbouring tiles that see a changed halo (and the tile itself
@@ -658,14 +662,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) recon_dense_kernel(SweepPar
     }
 }
 
-// Persistent propagation. Warp w owns a contiguous run of tiles (tiles are
-// numbered column by column, so a run is a vertical strip); it visits those
-// flagged, and leaves when nothing is flagged or being visited anywhere. A
-// visit is counted in `pending` from the moment its tile is flagged until
+// Persistent propagation. The tiles (numbered column by column) are cut into
+// segments of `seg` tiles (a vertical strip each; up to kSegMax, and about
+// the tiles per warp when there are fewer), dealt to the warps in turn:
+// segment s belongs to warp s mod nw. A warp visits the flagged tiles of its
+// segments in order, so a change flows down a strip within one pass over
+// it; a warp with nothing flagged in its own segments takes flagged tiles
+// of another warp's (a different one each idle round), which keeps the
+// warps busy while the flagged tiles gather in a few regions. A tile is
+// taken by swapping its flag bits for kBusy and released after the visit.
+// A visit is counted in `pending` from the moment its tile is flagged until
 // after the visit has flagged its neighbours, so pending = 0 means the image
-// is at the fixed point. The launch is cooperative only to guarantee that
-// every warp is resident (a flagged tile's owner always runs).
+// is at the fixed point, and every warp leaves. The launch is cooperative
+// only to guarantee that every warp is resident.
 // QUEUE = 0: dense visits; QUEUE = 1: queue visits.
+constexpr int kSegMax = 8;
 template <int CONN, int QUEUE>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persistent_kernel(SweepParams p)
 {
@@ -690,51 +701,78 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
     const int gw = blockIdx.x * kWarpsPerCta + warp;
     const int nw = gridDim.x * kWarpsPerCta;
     const int n = p.nvirt ? (int)*p.nvirt : p.ntiles;
-    const int chunk = (n + nw - 1) / nw;
-    const int own0 = gw * chunk;
-    const int own1 = min(n, own0 + chunk);
+    const int seg = max(1, min(kSegMax, n / nw));
+    const int spb = 32 / seg;                     // segments per ballot
+    const int nseg = (n + seg - 1) / seg;
     const uint64_t t_start = globaltimer_ns();
     uint32_t nvisits = 0, work = 0;
     int idle = 0;
     bool stop = false;
     for (;;) {
         bool did = false;
-        for (int base = own0; base < own1 && !stop; base += 32) {
-            const int vl = base + lane;
-            const int tl = vl < own1 ? (p.map ? p.map[vl] : vl) : 0;
-            const bool f = vl < own1 && *reinterpret_cast<volatile uint32_t *>(p.flags + tl) != 0u;
-            uint32_t mask = __ballot_sync(0xffffffffu, f);
-            while (mask) {
-                const int i = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int t = __shfl_sync(0xffffffffu, tl, i);
-                uint32_t got = 0;
-                if (lane == 0) {
-                    // a visit starts only within the visit bound and before
-                    // any bound was reached; past one the propagation stops
-                    // short of the fixed point and says so
-                    if (*reinterpret_cast<volatile uint32_t *>(p.abort)) {
-                        got = 0xffffffffu;
-                    } else if (p.max_visits && atomicAdd(p.spent, 1u) >= p.max_visits) {
-                        raise_status(p.err, RT_ETIMEOUT);
-                        atomicExch(p.abort, 1u);
-                        got = 0xffffffffu;
-                    } else {
-                        got = atomicExch(p.flags + t, 0u);
+        // the own segments, spb per ballot; with nothing flagged there,
+        // another warp's
+        for (int attempt = 0; attempt < 2 && !did && !stop; ++attempt) {
+            int owner = gw;
+            if (attempt == 1) {
+                if (nw == 1) break;
+                owner = (int)(((int64_t)gw + 1 + (int64_t)idle * 613) % nw);
+                if (owner == gw) owner = (owner + 1) % nw;
+            }
+            for (int s0 = owner; s0 < nseg && !stop; s0 += spb * nw) {
+                const int sl = lane / seg;
+                const int sg = s0 + sl * nw;
+                const int vl = sg * seg + lane % seg;
+                const bool in = sl < spb && sg < nseg && vl < n;
+                const int tl = in ? (p.map ? p.map[vl] : vl) : 0;
+                const uint32_t fv = in ? *reinterpret_cast<volatile uint32_t *>(p.flags + tl) : 0u;
+                uint32_t mask = __ballot_sync(0xffffffffu, (fv & ~kBusy) != 0u && !(fv & kBusy));
+                while (mask) {
+                    const int i = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const int t = __shfl_sync(0xffffffffu, tl, i);
+                    uint32_t cur = __shfl_sync(0xffffffffu, fv, i);
+                    uint32_t got = 0;
+                    if (lane == 0) {
+                        // a visit starts only within the visit bound and before
+                        // any bound was reached; past one the propagation stops
+                        // short of the fixed point and says so
+                        if (*reinterpret_cast<volatile uint32_t *>(p.abort)) {
+                            got = 0xffffffffu;
+                        } else if (p.max_visits && atomicAdd(p.spent, 1u) >= p.max_visits) {
+                            raise_status(p.err, RT_ETIMEOUT);
+                            atomicExch(p.abort, 1u);
+                            got = 0xffffffffu;
+                        } else {
+                            // the flag bits for kBusy, unless another warp is
+                            // visiting the tile or took its flag (then skip it)
+                            for (int k = 0; k < 16; ++k) {
+                                if ((cur & kBusy) || !(cur & ~kBusy)) break;
+                                const uint32_t prev = atomicCAS(p.flags + t, cur, kBusy);
+                                if (prev == cur) {
+                                    got = cur;
+                                    break;
+                                }
+                                cur = prev;
+                            }
+                        }
                     }
+                    got = __shfl_sync(0xffffffffu, got, 0);
+                    if (got == 0xffffffffu) {
+                        stop = true;
+                        break;
+                    }
+                    if (!got) continue;
+                    __threadfence();
+                    if (QUEUE) work += visit_queue<CONN>(p, t, got, qb, lane);
+                    else work += visit_tile<CONN>(p, t, got, wb, lane);
+                    if (lane == 0) {
+                        atomicAnd(p.flags + t, ~kBusy);
+                        atomicSub(p.pending, 1u);
+                    }
+                    did = true;
+                    ++nvisits;
                 }
-                got = __shfl_sync(0xffffffffu, got, 0);
-                if (got == 0xffffffffu) {
-                    stop = true;
-                    break;
-                }
-                if (!got) continue;
-                __threadfence();
-                if (QUEUE) work += visit_queue<CONN>(p, t, got, qb, lane);
-                else work += visit_tile<CONN>(p, t, got, wb, lane);
-                if (lane == 0) atomicSub(p.pending, 1u);
-                did = true;
-                ++nvisits;
             }
         }
         if (stop) break;
