@@ -377,6 +377,33 @@ RT_API rt_status rt_tile_features(rt_ctx *ctx, const uint8_t *const *imgs, const
 RT_API rt_status rt_mlp_forward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, int B,
                                 float *logits, float *act, int32_t *pick, float min_prob, int fallback,
                                 void *stream);
+/*
+ * rt_mlp_forward_tc: the forward of rt_mlp_forward on the tensor cores, for
+ * training batches (the paper's PATS scheduler needs an estimate per task,
+ * Section 3.2.1; the network and its training are this library's). Three
+ * products of 128 samples per thread block with fp32 accumulators in tensor
+ * memory; their operands are bf16: the parameters, and the normalised input
+ * and both hidden layers rounded to nearest even. Outputs as in
+ * rt_mlp_forward; act holds the hidden layers in fp32 before that rounding.
+ * The rounding makes logits differ from rt_mlp_forward's by about 2^-8
+ * relative. dev_status (device int32, nullable) gets RT_ETIMEOUT if a
+ * product does not complete within its wait bound.
+ */
+RT_API rt_status rt_mlp_forward_tc(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, int B,
+                                   float *logits, float *act, int32_t *pick, float min_prob, int fallback,
+                                   int32_t *dev_status, void *stream);
+/*
+ * rt_mlp_backward_tc: the gradient of rt_mlp_backward on the tensor cores,
+ * from the act and logits of rt_mlp_forward_tc. Per block of 128 samples,
+ * dh1 = (dh2 W2) * [h1 > 0] and the W1, b1, W2, b2 gradients are bf16
+ * products with fp32 accumulators (dh2, dh1, h1 and the normalised input
+ * rounded to bf16); dz, dh2 and the W3, b3 gradients stay fp32. The blocks'
+ * partial sums are added in a fixed order, so the result is deterministic.
+ * Uses the context's workspace; dev_status as for rt_mlp_forward_tc.
+ */
+RT_API rt_status rt_mlp_backward_tc(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x,
+                                    const float *act, const float *logits, const int32_t *label, int B,
+                                    float *grad, float *loss, int32_t *dev_status, void *stream);
 RT_API rt_status rt_mlp_backward(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x,
                                  const float *act, const float *logits, const int32_t *label, int B,
                                  float *grad, float *loss, void *stream);

@@ -319,23 +319,37 @@ class Picker:
         self.norm = norm
 
     def forward(self, x: torch.Tensor, with_act: bool = False, min_prob: float = 0.0, fallback: int = 3,
-                stream=None):
+                stream=None, tensor_cores: bool = False, status=None):
         """Logits, saved activations (with_act) and picks; a pick whose
-        softmax probability is below min_prob becomes `fallback`."""
+        softmax probability is below min_prob becomes `fallback`.
+        tensor_cores: the tensor-core forward (bf16 operands, for training
+        batches); status: its device status word (int32, nullable)."""
         B = x.shape[0]
         logits = torch.empty((B, 3), dtype=torch.float32, device=self.device)
         act = torch.empty((B, 128), dtype=torch.float32, device=self.device) if with_act else None
         pick = torch.empty(B, dtype=torch.int32, device=self.device)
-        _check(lib().rt_mlp_forward(self.ctx.handle, self.wb.data_ptr(), self.norm.data_ptr(), x.contiguous().data_ptr(),
-                                    B, logits.data_ptr(), None if act is None else act.data_ptr(), pick.data_ptr(),
-                                    float(min_prob), int(fallback), _stream(stream)), "rt_mlp_forward")
+        args = (self.ctx.handle, self.wb.data_ptr(), self.norm.data_ptr(), x.contiguous().data_ptr(), B,
+                logits.data_ptr(), None if act is None else act.data_ptr(), pick.data_ptr(), float(min_prob),
+                int(fallback))
+        if tensor_cores:
+            _check(lib().rt_mlp_forward_tc(*args, None if status is None else status.data_ptr(), _stream(stream)),
+                   "rt_mlp_forward_tc")
+        else:
+            _check(lib().rt_mlp_forward(*args, _stream(stream)), "rt_mlp_forward")
         return logits, act, pick
 
-    def backward(self, x, act, logits, label, stream=None):
-        _check(lib().rt_mlp_backward(self.ctx.handle, self.wb.data_ptr(), self.norm.data_ptr(), x.contiguous().data_ptr(),
-                                     act.data_ptr(), logits.data_ptr(), label.to(torch.int32).contiguous().data_ptr(),
-                                     x.shape[0], self.grad.data_ptr(), self.loss.data_ptr(), _stream(stream)),
-               "rt_mlp_backward")
+    def backward(self, x, act, logits, label, stream=None, tensor_cores: bool = False, status=None):
+        """Gradient (into self.grad) and loss of the batch; tensor_cores: the
+        tensor-core backward (bf16 operands), from a tensor-core forward's
+        act and logits."""
+        args = (self.ctx.handle, self.wb.data_ptr(), self.norm.data_ptr(), x.contiguous().data_ptr(), act.data_ptr(),
+                logits.data_ptr(), label.to(torch.int32).contiguous().data_ptr(), x.shape[0], self.grad.data_ptr(),
+                self.loss.data_ptr())
+        if tensor_cores:
+            _check(lib().rt_mlp_backward_tc(*args, None if status is None else status.data_ptr(), _stream(stream)),
+                   "rt_mlp_backward_tc")
+        else:
+            _check(lib().rt_mlp_backward(*args, _stream(stream)), "rt_mlp_backward")
         return self.grad, self.loss
 
     def step(self, lr=3e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4, stream=None):

@@ -18,7 +18,7 @@ EXPORTS = (
     "rt_create", "rt_destroy", "rt_status_str", "rt_version", "rt_workspace_bytes", "rt_marker",
     "rt_reconstruct", "rt_fill_holes", "rt_label_area", "rt_edt", "rt_seg_params_default",
     "rt_segment_batch", "rt_timing_enable", "rt_timing_read", "rt_kernel_launches", "rt_recon_stats",
-    "rt_edt_noalloc", "rt_synth_tile", "rt_tile_features", "rt_mlp_forward", "rt_mlp_backward",
+    "rt_edt_noalloc", "rt_synth_tile", "rt_tile_features", "rt_mlp_forward", "rt_mlp_forward_tc", "rt_mlp_backward", "rt_mlp_backward_tc",
     "rt_mlp_adamw", "rt_set_picker", "rt_last_picks", "rt_set_limits", "rt_segment_workspace_bytes",
     "rt_feature_norm", "rt_watershed", "rt_object_features", "rt_set_picker_classes", "rt_set_queue_capacity",
 )
@@ -91,6 +91,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_tile_features.restype = _int
     lib.rt_mlp_forward.argtypes = [_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, ctypes.c_float, _int, _vp]
     lib.rt_mlp_forward.restype = _int
+    lib.rt_mlp_forward_tc.argtypes = [_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, ctypes.c_float, _int, _vp, _vp]
+    lib.rt_mlp_forward_tc.restype = _int
+    lib.rt_mlp_backward_tc.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp]
+    lib.rt_mlp_backward_tc.restype = _int
     lib.rt_mlp_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp]
     lib.rt_mlp_backward.restype = _int
     _f = ctypes.c_float

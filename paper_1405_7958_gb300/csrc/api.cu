@@ -947,6 +947,16 @@ rt_status rt_mlp_forward(rt_ctx *ctx, const uint16_t *wb, const float *norm, con
     return cuda_status(launch_mlp_forward(wb, norm, x, B, logits, act, pick, min_prob, fallback, (cudaStream_t)stream));
 }
 
+rt_status rt_mlp_forward_tc(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, int B, float *logits,
+                            float *act, int32_t *pick, float min_prob, int fallback, int32_t *dev_status, void *stream)
+{
+    if (!ctx || !wb || !norm || !x || B < 1 || !(min_prob <= 1.0f) || fallback < 0) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    ctx->launches += 1;
+    return cuda_status(
+        launch_mlp_forward_tc(wb, norm, x, B, logits, act, pick, min_prob, fallback, dev_status, (cudaStream_t)stream));
+}
+
 rt_status rt_set_picker_classes(rt_ctx *ctx, const int *variants, const int *max_locals)
 {
     if (!ctx || !variants || !max_locals) return RT_EINVAL;
@@ -971,6 +981,19 @@ rt_status rt_mlp_backward(rt_ctx *ctx, const uint16_t *wb, const float *norm, co
     ctx->launches += 2;
     return cuda_status(launch_mlp_backward(wb, norm, x, act, logits, label, B, grad, loss, (float *)ctx->ws,
                                            (cudaStream_t)stream));
+}
+
+rt_status rt_mlp_backward_tc(rt_ctx *ctx, const uint16_t *wb, const float *norm, const float *x, const float *act,
+                             const float *logits, const int32_t *label, int B, float *grad, float *loss,
+                             int32_t *dev_status, void *stream)
+{
+    if (!ctx || !wb || !norm || !x || !act || !logits || !label || !grad || B < 1) return RT_EINVAL;
+    DeviceGuard g(ctx->device);
+    rt_status st = ensure_ws(ctx, mlp_backward_tc_workspace_bytes(B));
+    if (st != RT_OK) return st;
+    ctx->launches += 2;
+    return cuda_status(launch_mlp_backward_tc(wb, norm, x, act, logits, label, B, grad, loss, (float *)ctx->ws,
+                                              dev_status, (cudaStream_t)stream));
 }
 
 rt_status rt_feature_norm(rt_ctx *ctx, const float *x, int B, float *norm, void *stream)

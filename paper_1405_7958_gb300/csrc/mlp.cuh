@@ -21,7 +21,21 @@ constexpr int kMlpDelta = kMlpOut + 2 * kMlpH + kMlpIn + 1;   // dz, dh2, dh1, x
 // probability is below min_prob (min_prob <= 0: never)
 cudaError_t launch_mlp_forward(const uint16_t *wb, const float *norm, const float *x, int B, float *logits, float *act,
                                int32_t *pick, float min_prob, int fallback, cudaStream_t s);
+// the same forward on the tensor cores (mlp_tc.cu): bf16 operands (the
+// normalised input and the hidden layers rounded to bf16), fp32 accumulation
+// in tensor memory, 128 samples per CTA; err (nullable) gets RT_ETIMEOUT if a
+// product does not complete within its wait bound
+cudaError_t launch_mlp_forward_tc(const uint16_t *wb, const float *norm, const float *x, int B, float *logits,
+                                  float *act, int32_t *pick, float min_prob, int fallback, int32_t *err,
+                                  cudaStream_t s);
 size_t mlp_backward_workspace_bytes(int B);
+// the backward on the tensor cores (mlp_tc.cu): dh1 and the W1, b1, W2, b2
+// gradients as bf16 products with fp32 accumulation, W3 and b3 in fp32;
+// deterministic (fixed-order sums of per-CTA partials)
+size_t mlp_backward_tc_workspace_bytes(int B);
+cudaError_t launch_mlp_backward_tc(const uint16_t *wb, const float *norm, const float *x, const float *act,
+                                   const float *logits, const int32_t *label, int B, float *grad, float *loss,
+                                   float *ws, int32_t *err, cudaStream_t s);
 cudaError_t launch_mlp_backward(const uint16_t *wb, const float *norm, const float *x, const float *act,
                                 const float *logits, const int32_t *label, int B, float *grad, float *loss, float *ws,
                                 cudaStream_t s);

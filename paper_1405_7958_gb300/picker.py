@@ -9,8 +9,10 @@ are timings the method itself produces: every tile is drawn on the GPU,
 segmented with each schedule and with the plain one (CUDA events on the
 launch stream, median of `reps` runs), and checked to give the same labels
 and distances under all four; the label is the fastest of the three.
-Training runs the library's own forward, backward, AdamW and normalisation
-kernels; torch only holds the buffers.
+Training runs the library's own kernels: the tensor-core forward and
+backward (tcgen05, bf16 operands, fp32 accumulation), AdamW and the input
+normalisation; torch only holds the buffers. The picks (evaluation and the
+segmentation chain) come from the fp32 forward.
 
 The robustness study (the paper's PATS evaluation perturbs the speedup
 estimates its scheduler relies on, Section 5.5) adds Gaussian noise of
@@ -114,7 +116,7 @@ def build_dataset(n: int, seed: int, reps: int = 3, ctx=None, log_every: int = 5
 def train(feats: np.ndarray, times: np.ndarray, epochs: int = 60, batch: int = 256, lr: float = 3e-3,
           seed: int = 0, device=None) -> rt.Picker:
     """Cross-entropy on the fastest of the three classes, mini-batch AdamW,
-    all on the GPU."""
+    all on the GPU (forward and backward on the tensor cores)."""
     device = device or torch.device("cuda", torch.cuda.current_device())
     x = torch.from_numpy(np.ascontiguousarray(feats)).to(device)
     y = torch.from_numpy(times[:, :PLAIN].argmin(axis=1).astype(np.int32)).to(device)
@@ -127,8 +129,8 @@ def train(feats: np.ndarray, times: np.ndarray, epochs: int = 60, batch: int = 2
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
             xb, yb = x[idx].contiguous(), y[idx].contiguous()
-            logits, act, _ = pk.forward(xb, with_act=True)
-            pk.backward(xb, act, logits, yb)
+            logits, act, _ = pk.forward(xb, with_act=True, tensor_cores=True)
+            pk.backward(xb, act, logits, yb, tensor_cores=True)
             pk.step(lr=lr)
     return pk
 

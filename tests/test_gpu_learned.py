@@ -103,6 +103,87 @@ def test_mlp_forward_small_and_large_batches_agree(rt):
         assert torch.equal(pick, big_pick[:n])
 
 
+def _bf16_round(a):
+    """Round float32 values to bf16 (nearest even), as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("B", [1, 128, 300, 2000])
+def test_mlp_forward_tensor_cores_match_oracle(rt, B):
+    """The tensor-core forward against the fp64 oracle network evaluated on
+    the same bf16 operands: the normalised input (computed in fp32, as the
+    kernel does) rounded to bf16, and each hidden layer rounded to bf16
+    before it enters the next product. Accumulation order and fp32 sums may
+    flip a hidden value across a bf16 rounding boundary, so the hidden
+    layers compare within 1e-2 of their scale; the first hidden layer, whose
+    inputs are rounded identically on both sides, within 1e-5. Batches of 1,
+    128 and ragged 300 and 2000 samples (several thread blocks, partial
+    last block)."""
+    rng = np.random.default_rng(5)
+    pk = rt.Picker(seed=7)
+    norm = np.concatenate([rng.normal(size=24), rng.uniform(0.5, 2.0, size=24)]).astype(np.float32)
+    pk.norm = torch.from_numpy(norm).cuda()
+    x, _ = _picker_inputs(rng, B)
+    xd = torch.from_numpy(x).cuda()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    logits, act, pick = pk.forward(xd, with_act=True, tensor_cores=True, status=st)
+    assert int(host(st)[0]) == 0
+    w = OM.unflatten(OM.bf16_bits_to_f64(host(pk.wb)))
+    xn = _bf16_round((x - norm[:24]) / norm[24:])
+    h1 = np.maximum(xn @ w["W1"].T + w["b1"], 0.0)
+    got = host(act)
+    scale1 = np.abs(h1).max() + 1e-30
+    assert np.abs(got[:, :64] - h1).max() <= 1e-5 * scale1
+    h2 = np.maximum(_bf16_round(got[:, :64]) @ w["W2"].T + w["b2"], 0.0)
+    assert np.abs(got[:, 64:] - h2).max() <= 1e-5 * (np.abs(h2).max() + 1e-30)
+    z = _bf16_round(got[:, 64:]) @ w["W3"].T + w["b3"]
+    zl = host(logits)
+    assert np.abs(zl - z).max() <= 1e-5 * (np.abs(z).max() + 1e-30)
+    assert np.array_equal(host(pick), zl.argmax(axis=1))
+    # against the fp32 forward: the same network up to the bf16 operand rounding
+    l32, a32, p32 = pk.forward(xd, with_act=True)
+    a32 = host(a32)
+    assert np.abs(got - a32).max() <= 1e-2 * (np.abs(a32).max() + 1e-30)
+    assert np.abs(zl - host(l32)).max() <= 2e-2 * (np.abs(host(l32)).max() + 1e-30)
+
+
+@pytest.mark.parametrize("B", [1, 256, 777])
+def test_mlp_backward_tensor_cores_match_oracle(rt, B):
+    """The tensor-core backward against the fp64 oracle gradient (relative
+    2e-2 per parameter tensor, cosine above 0.999, as for the fp32 backward:
+    the deltas and activations enter its products as bf16), and against the
+    fp32 backward on the same forward outputs (relative 1e-2); W3 and b3,
+    computed in fp32 on both paths, agree to 1e-5. Deterministic: a second
+    call gives the same bits. One, two and seven blocks of 128 samples."""
+    rng = np.random.default_rng(11)
+    pk = rt.Picker(seed=2)
+    norm = np.concatenate([rng.normal(size=24), rng.uniform(0.5, 2.0, size=24)]).astype(np.float32)
+    pk.norm = torch.from_numpy(norm).cuda()
+    x, y = _picker_inputs(rng, B)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    logits, act, _ = pk.forward(xd, with_act=True, tensor_cores=True, status=st)
+    grad, loss = pk.backward(xd, act, logits, yd, tensor_cores=True, status=st)
+    g_tc, l_tc = host(grad).astype(np.float64).copy(), float(host(loss)[0])
+    pk.backward(xd, act, logits, yd, tensor_cores=True, status=st)
+    assert np.array_equal(host(grad), g_tc.astype(np.float32)) and int(host(st)[0]) == 0
+    grad32, loss32 = pk.backward(xd, act, logits, yd)
+    g_32 = host(grad32).astype(np.float64)
+    assert np.isclose(l_tc, float(host(loss32)[0]), rtol=1e-6)
+    p = OM.bf16_bits_to_f64(host(pk.wb))
+    g_want = OM.backward(p, norm, x, y)
+    for name, _ in OM.SHAPES:
+        a, w, c = (OM.unflatten(v)[name].ravel() for v in (g_tc, g_want, g_32))
+        assert np.linalg.norm(a - w) <= 2e-2 * np.linalg.norm(w) + 1e-7, name
+        if np.linalg.norm(w) > 0:
+            assert a @ w / (np.linalg.norm(a) * np.linalg.norm(w)) > 0.999, name
+        tol = 1e-5 if name in ("W3", "b3") else 1e-2
+        assert np.linalg.norm(a - c) <= tol * np.linalg.norm(c) + 1e-7, name
+    assert np.isclose(l_tc, OM.loss(p, norm, x, y), rtol=1e-2)
+
+
 def test_adamw_step_matches_oracle(rt):
     rng = np.random.default_rng(2)
     pk = rt.Picker(seed=3)
@@ -121,6 +202,8 @@ def test_adamw_step_matches_oracle(rt):
 
 
 def test_training_reduces_loss(rt):
+    """Training with the tensor-core forward and backward and AdamW fits a
+    separable labelling."""
     rng = np.random.default_rng(4)
     x = rng.normal(size=(512, 24)).astype(np.float32)
     y = (x[:, 0] > 0.3).astype(np.int32) + (x[:, 1] > 0.8).astype(np.int32)
@@ -129,8 +212,8 @@ def test_training_reduces_loss(rt):
     pk.set_norm(xd)
     losses = []
     for _ in range(150):
-        logits, act, _ = pk.forward(xd, with_act=True)
-        _, loss = pk.backward(xd, act, logits, yd)
+        logits, act, _ = pk.forward(xd, with_act=True, tensor_cores=True)
+        _, loss = pk.backward(xd, act, logits, yd, tensor_cores=True)
         losses.append(float(loss.item()))
         pk.step(lr=1e-2)
     assert losses[-1] < 0.5 * losses[0]
