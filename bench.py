@@ -503,6 +503,30 @@ def objects_leg(rt, ctx, outs, imgs):
             "features_per_nucleus": 20, "watershed_h": 2}
 
 
+def picker_train_leg(rt, dev, B=256):
+    """One training step of the picker network (forward with saved
+    activations, backward, AdamW) on a batch of B samples, on the tensor
+    cores and on the fp32 kernels; median of 50 after 5 warm-up steps."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(3)
+    x = (torch.randn(B, 24, generator=g) * 3 + 1).to(dev)
+    y = torch.randint(0, 3, (B,), generator=g, dtype=torch.int32).to(dev)
+    res = {"batch": B}
+    for name, tc in (("tensor_cores_us", True), ("fp32_us", False)):
+        pk = rt.Picker(device=dev, seed=1)
+        pk.set_norm(x)
+
+        def step():
+            logits, act, _ = pk.forward(x, with_act=True, tensor_cores=tc)
+            pk.backward(x, act, logits, y, tensor_cores=tc)
+            pk.step()
+
+        for _ in range(5):
+            step()
+        res[name] = timed_ms(step, 50) * 1000.0
+    return res
+
+
 def slide_leg(rt, ctx, side=16384):
     """Whole-slide segmentation: one side x side slide (16 tiles of 4096^2,
     nuclei across every seam) as one image; median of 3 after a warm-up."""
@@ -607,6 +631,7 @@ def run_native(a, rank, world, local_rank):
     config3 = None
     objects = None
     slide = None
+    train_step = None
     stream = torch.cuda.current_stream()
     if not a.no_configs and world == 1:
         import synth
@@ -630,6 +655,7 @@ def run_native(a, rank, world, local_rank):
         config3 = config3_leg(rt, ctx, dev, lambda: torch.cuda.Stream(device=dev))
         objects = objects_leg(rt, ctx, outs_l[0], imgs)
         slide = slide_leg(rt, ctx)
+        train_step = picker_train_leg(rt, dev)
 
     serving = None
     if a.serve_seconds > 0 and world == 1:
@@ -796,6 +822,7 @@ def run_native(a, rank, world, local_rank):
             "config3_uneven_64_graph": config3,
             "objects_per_tile": objects,
             "slide": slide,
+            "picker_train_step": train_step,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -424,29 +424,36 @@ __global__ void __launch_bounds__(kTcM) mlp_backward_tc_kernel(const uint16_t *w
     if (!ok && t == 0) raise_status(err, RT_ETIMEOUT);
 }
 
-// the gradient: W1, b1, W2, b2 as the sum of the CTAs' partials (in CTA
-// order); W3, b3 over the samples from dz and h2 (fp32, in sample order);
-// thread kMlpParams sums the loss
+// the gradient, one warp per parameter: W1, b1, W2, b2 as the sum of the
+// CTAs' partials, W3 and b3 over the samples from dz and h2 (fp32); the last
+// warp sums the loss. Lane l adds the terms l, l + 32, ... in order, then a
+// fixed butterfly adds the lanes, so the result does not depend on
+// scheduling.
 __global__ void mlp_grad_tc_kernel(const float *part, int nblk, const float *dz, const float *act, const float *lossb,
                                    int B, float *grad, float *loss)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (p > kMlpParams) return;
     float s = 0.f;
     if (p == kMlpParams) {
-        for (int b = 0; b < B; ++b) s += lossb[b];
-        if (loss) *loss = s / (float)B;
-        return;
-    }
-    if (p < kW3) {
-        for (int k = 0; k < nblk; ++k) s += part[(int64_t)k * kBwPart + p];
+        for (int b = lane; b < B; b += 32) s += lossb[b];
+    } else if (p < kW3) {
+        for (int k = lane; k < nblk; k += 32) s += part[(int64_t)k * kBwPart + p];
     } else if (p < kB3) {
         const int k = (p - kW3) / kMlpH, j = (p - kW3) % kMlpH;
-        for (int b = 0; b < B; ++b) s = fmaf(dz[(int64_t)b * kMlpOut + k], act[(int64_t)b * kMlpAct + kMlpH + j], s);
+        for (int b = lane; b < B; b += 32)
+            s = fmaf(dz[(int64_t)b * kMlpOut + k], act[(int64_t)b * kMlpAct + kMlpH + j], s);
     } else {
-        for (int b = 0; b < B; ++b) s += dz[(int64_t)b * kMlpOut + (p - kB3)];
+        for (int b = lane; b < B; b += 32) s += dz[(int64_t)b * kMlpOut + (p - kB3)];
     }
-    grad[p] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane != 0) return;
+    if (p == kMlpParams) {
+        if (loss) *loss = s / (float)B;
+    } else {
+        grad[p] = s;
+    }
 }
 
 }  // namespace
@@ -470,8 +477,8 @@ cudaError_t launch_mlp_backward_tc(const uint16_t *wb, const float *norm, const 
     if (e != cudaSuccess) return e;
     mlp_backward_tc_kernel<<<nblk, kTcM, kBwSmem, s>>>(wb, norm, x, act, logits, label, B, part, dz, lossb, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mlp_grad_tc_kernel<<<(unsigned)ceil_div(kMlpParams + 1, 128), 128, 0, s>>>(part, nblk, dz, act, lossb, B, grad,
-                                                                                 loss);
+    mlp_grad_tc_kernel<<<(unsigned)ceil_div((int64_t)(kMlpParams + 1) * 32, 256), 256, 0, s>>>(part, nblk, dz, act,
+                                                                                               lossb, B, grad, loss);
     return cudaGetLastError();
 }
 
