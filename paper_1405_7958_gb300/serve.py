@@ -184,6 +184,12 @@ def run_batched(reqs, pool, budget_bytes: int = 40 << 30, max_batch: int = 32, n
     ctxs = [rt.Context(workspace_bytes=reserve) for _ in range(n_streams)]
     held = [c.workspace_bytes() for c in ctxs]
     budget_bytes -= sum(held)
+    # The requests' device buffers come from torch's caching allocator. One
+    # block of the whole remaining budget, allocated and freed here, stays in
+    # its cache, so no allocation inside the loop reaches cudaMalloc, which
+    # would wait for every stream's work to finish.
+    if budget_bytes > 0:
+        torch.empty(budget_bytes, dtype=torch.uint8, device="cuda")
     if picker is not None:
         for c in ctxs:
             picker.attach(c)
