@@ -734,14 +734,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
                     uint32_t cur = __shfl_sync(0xffffffffu, fv, i);
                     uint32_t got = 0;
                     if (lane == 0) {
-                        // a visit starts only within the visit bound and before
-                        // any bound was reached; past one the propagation stops
-                        // short of the fixed point and says so
                         if (*reinterpret_cast<volatile uint32_t *>(p.abort)) {
-                            got = 0xffffffffu;
-                        } else if (p.max_visits && atomicAdd(p.spent, 1u) >= p.max_visits) {
-                            raise_status(p.err, RT_ETIMEOUT);
-                            atomicExch(p.abort, 1u);
                             got = 0xffffffffu;
                         } else {
                             // the flag bits for kBusy, unless another warp is
@@ -754,6 +747,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
                                     break;
                                 }
                                 cur = prev;
+                            }
+                            // a visit starts only within the visit bound; past
+                            // it the tile gets its flag back and the
+                            // propagation stops short of the fixed point and
+                            // says so
+                            if (got && p.max_visits && atomicAdd(p.spent, 1u) >= p.max_visits) {
+                                atomicOr(p.flags + t, got);
+                                atomicAnd(p.flags + t, ~kBusy);
+                                raise_status(p.err, RT_ETIMEOUT);
+                                atomicExch(p.abort, 1u);
+                                got = 0xffffffffu;
                             }
                         }
                     }
