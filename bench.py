@@ -419,7 +419,8 @@ def config3_leg(rt, ctx, dev, stream_ctor):
     b3 = [rt.synth_tile(H, W, sd, ns, ctx=ctx) for H, W, ns, sd in specs]
     px3 = sum(H * W for H, W, _, _ in specs)
     tuned = autotune.tune(b3, reps=2, ctx=ctx)["best"]
-    p3 = rt.SegParams(variant=int(tuned["variant"]), max_local=int(tuned["max_local"]))
+    p3 = rt.SegParams(variant=int(tuned["variant"]), max_local=int(tuned["max_local"]),
+                      strip_tiles=int(tuned["strip_tiles"]))
     g3s = stream_ctor()
     with torch.cuda.stream(g3s):
         o3 = rt.segment_batch(b3, p3, ctx=ctx, stream=g3s, want_recon=False, want_filled=False)

@@ -482,6 +482,10 @@ typedef struct {
     int pick_min_prob; /* learned policy: the network's pick stands only when its softmax
                           probability is at least pick_min_prob / 1000; below, the tile runs
                           the plain schedule (`variant`, `max_local`). 0 = always the pick */
+    int strip_tiles; /* raster propagation: tiles of 32 x 64 per strip, the block of
+                        vertically adjacent tiles one warp owns (1..32; strips are dealt to
+                        the warps in turn); 0 = the library's choice (up to 8, about the
+                        tiles per warp). Any value gives the same output */
 } rt_seg_params;
 
 enum { RT_POLICY_PLAIN = 0, RT_POLICY_LEARNED = 1 };

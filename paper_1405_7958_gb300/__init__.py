@@ -407,6 +407,7 @@ class SegParams:
     max_iters: int = 0       # tile visits per tile allowed to the propagation (0: the context's bound)
     timeout_ms: int = 0      # device-time bound of each propagation (0: the context's)
     pick_min_prob: int = 0   # learned: a pick stands only at softmax probability >= this / 1000
+    strip_tiles: int = 0     # tiles per warp strip of the raster propagation (0: the library's choice)
 
     def to_c(self) -> _native.RtSegParams:
         p = _native.RtSegParams()

@@ -49,7 +49,7 @@ class RtTile(ctypes.Structure):
 class RtSegParams(ctypes.Structure):
     _fields_ = [(n, _int) for n in ("h_offset", "threshold", "min_area", "max_area", "conn_recon",
                                     "conn_fill", "variant", "max_local", "policy", "max_iters", "timeout_ms",
-                                    "pick_min_prob")]
+                                    "pick_min_prob", "strip_tiles")]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:

@@ -1,10 +1,12 @@
 """Autotuner for the batched segmentation chain.
 
 The run-time knobs of the reconstruction are the propagation variant (the
-raster sweeps, the hybrid's per-tile queues, the global frontier queues)
-and the budget of sweep iterations per dense tile visit (`max_local`): a small
+raster sweeps, the hybrid's per-tile queues, the global frontier queues),
+the budget of sweep iterations per dense tile visit (`max_local`: a small
 budget revisits tiles more often, a large one sweeps tiles longer before
-their neighbours' news arrives. The tuner times each candidate on the batch
+their neighbours' news arrives), and the raster propagation's strip of
+tiles per warp (`strip_tiles`: a longer strip carries a change further down
+in one pass over it, a shorter one spreads each warp's tiles wider). The tuner times each candidate on the batch
 itself (CUDA events on the launch stream, median of `reps`), keeps the
 fastest, and caches the choice per size class in a JSON table.
 """
@@ -18,7 +20,8 @@ import torch
 
 import paper_1405_7958_gb300 as rt
 
-CANDIDATES = tuple((v, m) for v in (rt.RT_RASTER,) for m in (4, 8, 12, 16)) + ((rt.RT_HYBRID, 0), (rt.RT_FRONTIER, 0))
+CANDIDATES = tuple((rt.RT_RASTER, m, st) for m in (8, 12, 16) for st in (4, 8, 16)) + (
+    (rt.RT_HYBRID, 0, 0), (rt.RT_FRONTIER, 0, 0))
 
 
 def size_class(images) -> str:
@@ -33,8 +36,8 @@ def tune(images, reps: int = 3, candidates=CANDIDATES, ctx=None, stream=None) ->
     outs = None
     best = None
     results = []
-    for v, m in candidates:
-        p = rt.SegParams(variant=v, max_local=m)
+    for v, m, st in candidates:
+        p = rt.SegParams(variant=v, max_local=m, strip_tiles=st)
         outs = rt.segment_batch(images, p, outputs=outs, ctx=ctx, stream=stream)   # warm-up
         ts = []
         for _ in range(reps):
@@ -45,7 +48,7 @@ def tune(images, reps: int = 3, candidates=CANDIDATES, ctx=None, stream=None) ->
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
         t = float(np.median(ts))
-        results.append({"variant": v, "max_local": m, "ms": t})
+        results.append({"variant": v, "max_local": m, "strip_tiles": st, "ms": t})
         if best is None or t < best["ms"]:
             best = results[-1]
     return {"best": best, "all": results}
@@ -68,4 +71,5 @@ class Table:
             with open(self.path, "w") as fh:
                 json.dump(self.t, fh, indent=1)
         b = self.t[key]
-        return rt.SegParams(variant=int(b["variant"]), max_local=int(b["max_local"]))
+        return rt.SegParams(variant=int(b["variant"]), max_local=int(b["max_local"]),
+                            strip_tiles=int(b.get("strip_tiles", 0)))

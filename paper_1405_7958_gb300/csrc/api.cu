@@ -228,6 +228,7 @@ void carve_recon(Carve &cv, ReconBatch &b, ReconWs &w, bool grouped = false, uin
 struct Limits {
     int max_iters;
     uint64_t timeout_ns;
+    int strip = 0;   // tiles per warp strip of the raster propagation (0: the library's choice)
 };
 
 Limits ctx_limits(const rt_ctx *ctx) { return {ctx->max_iters, ctx->timeout_ns ? ctx->timeout_ns : kSweepTimeoutNs}; }
@@ -294,6 +295,7 @@ rt_status run_recon(rt_ctx *ctx, ReconBatch &b, ReconWs &w, int conn, int varian
     p.err = err;
     p.visits = w.ctl + kCtlVisits;
     p.timeout_ns = lim.timeout_ns;
+    p.seg_max = lim.strip;
     const int64_t bound = (int64_t)lim.max_iters * b.ntiles;
     p.max_visits = lim.max_iters > 0 ? (uint32_t)(bound < 0xffffffffLL ? bound : 0xffffffffLL) : 0u;
     p.spent = w.ctl + kCtlSpent;
@@ -385,6 +387,7 @@ bool bad_params(const rt_seg_params &P)
     if (P.variant < RT_AUTO || P.variant > RT_FRONTIER) return true;
     if (P.policy != RT_POLICY_PLAIN && P.policy != RT_POLICY_LEARNED) return true;
     if (P.max_local < 0 || P.max_iters < 0 || P.timeout_ms < 0) return true;
+    if (P.strip_tiles < 0 || P.strip_tiles > 32) return true;
     if (P.pick_min_prob < 0 || P.pick_min_prob > 1000) return true;
     return false;
 }
@@ -1055,6 +1058,7 @@ void rt_seg_params_default(rt_seg_params *p)
     p->max_iters = 0;
     p->timeout_ms = 0;
     p->pick_min_prob = 0;
+    p->strip_tiles = 0;
 }
 
 rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_seg_params *params, void *stream)
@@ -1071,6 +1075,7 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
     Limits lim = ctx_limits(ctx);
     if (P.max_iters > 0) lim.max_iters = P.max_iters;
     if (P.timeout_ms > 0) lim.timeout_ns = (uint64_t)P.timeout_ms * 1000000ull;
+    lim.strip = P.strip_tiles;
     // one allocation for the largest chunk, before anything is enqueued
     rt_status st = ensure_ws(ctx, segment_ws_bytes(tiles, n, P, learned, ctx));
     if (st != RT_OK) return st;

@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
     const int gw = blockIdx.x * kWarpsPerCta + warp;
     const int nw = gridDim.x * kWarpsPerCta;
     const int n = p.nvirt ? (int)*p.nvirt : p.ntiles;
-    const int seg = max(1, min(kSegMax, n / nw));
+    const int seg = p.seg_max > 0 ? min(p.seg_max, 32) : max(1, min(kSegMax, n / nw));
     const int spb = 32 / seg;                     // segments per ballot
     const int nseg = (n + seg - 1) / seg;
     const uint64_t t_start = globaltimer_ns();

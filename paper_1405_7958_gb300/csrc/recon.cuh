@@ -64,6 +64,7 @@ struct SweepParams {
     int32_t *err;             // device status word
     uint32_t *visits;         // [0] tile visits, [1] dense iterations, [2] queue pops (statistics)
     int max_local;            // local iterations per visit before revisiting
+    int seg_max;              // tiles per warp strip (0: up to kSegMax, about the tiles per warp)
     uint64_t timeout_ns;      // bound on the whole propagation (device time)
     uint32_t max_visits;      // bound on the tile visits of the propagation (0 = none)
     uint32_t *spent;          // visits started so far (device word, zeroed with the control words)

@@ -3,7 +3,8 @@ time bound that runs out stops the propagation with RT_ETIMEOUT and leaves
 the context usable (the next call gives the oracle's bytes); a batch of more
 than 32 uneven tiles (two chunks) eager and replayed from a CUDA graph,
 every tile against the oracle; a context reserved with the library's
-workspace figure never grows; the feature normalisation against numpy."""
+workspace figure never grows; the feature normalisation against numpy; the
+raster propagation's strip length changes no byte."""
 import numpy as np
 import pytest
 
@@ -180,3 +181,31 @@ def test_feature_norm_matches_numpy(rt):
     sd = np.maximum(xd.std(axis=0, ddof=1), 1e-6)
     assert np.allclose(norm[24:], sd, rtol=1e-6)
     assert norm[24 + 7] == np.float32(1e-6)
+
+
+@pytest.mark.parametrize("strip", [1, 3, 8, 16, 32])
+def test_strip_lengths_give_the_oracle_bytes(rt, strip):
+    """The raster propagation's strip of tiles per warp (rt_seg_params
+    strip_tiles, an autotuner knob) changes only which warp visits a tile
+    first: every length gives the oracle's bytes, on ragged tiles in one call
+    (a strip may cross from one image into the next) and on a spiral whose
+    front crosses many strips."""
+    shapes = [(700, 1031), (257, 300), (1100, 640)]
+    imgs = [synth.config2_tile(300 + i, H=H, W=W) for i, (H, W) in enumerate(shapes)]
+    outs = rt.segment_batch([dev(x) for x in imgs], rt.SegParams(strip_tiles=strip))
+    for o, x in zip(outs, imgs):
+        want = oracle.chain(x)
+        for k in ("R", "F", "L", "D"):
+            assert np.array_equal(host(o[k]), want[k]), k
+    I = synth.spiral(257, low=0)
+    (o,) = rt.segment_batch([dev(I)], rt.SegParams(strip_tiles=strip, h_offset=255))
+    J = np.zeros_like(I)
+    J[0, :], J[-1, :], J[:, 0], J[:, -1] = I[0, :], I[-1, :], I[:, 0], I[:, -1]
+    assert np.array_equal(host(o["R"]), oracle.recon(J, I, 8))
+
+
+def test_strip_length_out_of_range_is_rejected(rt):
+    x = dev(synth.config2_tile(5, H=64, W=64))
+    for bad in (-1, 33):
+        with pytest.raises(RuntimeError):
+            rt.segment_batch([x], rt.SegParams(strip_tiles=bad))
