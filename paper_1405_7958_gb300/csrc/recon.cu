@@ -716,7 +716,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, QUEUE ? 3 : 4) recon_persis
             int owner = gw;
             if (attempt == 1) {
                 if (nw == 1) break;
-                owner = (int)(((int64_t)gw + 1 + (int64_t)idle * 613) % nw);
+                // the next warp first, then pseudo-random others (a hash of
+                // the warp and the idle round, so every warp gets probed
+                // whatever the warp count)
+                const uint32_t h = idle ? ((uint32_t)gw * 0x9E3779B1u) ^ ((uint32_t)idle * 0x85EBCA77u) : 0u;
+                owner = (int)(((uint32_t)gw + 1u + (h >> 8)) % (uint32_t)nw);
                 if (owner == gw) owner = (owner + 1) % nw;
             }
             for (int s0 = owner; s0 < nseg && !stop; s0 += spb * nw) {
