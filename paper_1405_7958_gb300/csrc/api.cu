@@ -1097,10 +1097,9 @@ rt_status rt_segment_batch(rt_ctx *ctx, const rt_tile *tiles, int n, const rt_se
             const bool pick = picks_matter(ctx, P, cn);
             if (pick) {
                 Phase ph(ctx, RT_PHASE_PICK, s);
-                RT_CUDA_TRY(launch_features(c.fb, c.feat, s));
-                RT_CUDA_TRY(launch_mlp_forward(ctx->picker_wb, ctx->picker_norm, c.feat, cn, nullptr, nullptr, c.picks,
-                                               (float)P.pick_min_prob / 1000.0f, kPickClasses, s));
-                ctx->launches += 5;
+                RT_CUDA_TRY(launch_features_pick(c.fb, c.feat, ctx->picker_wb, ctx->picker_norm, c.picks,
+                                                 (float)P.pick_min_prob / 1000.0f, kPickClasses, s));
+                ctx->launches += 4;
             }
             st = run_recon(ctx, c.b, c.w, P.conn_recon, P.variant, P.max_local, c.w.err, s, lim,
                            pick ? c.picks : nullptr);

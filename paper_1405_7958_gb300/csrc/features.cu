@@ -15,6 +15,7 @@
 // left) give max min(Jd(q), D(p)) > Jd(p), and ln(1 + their count).
 // Counts are exact integers; the statistics are finished in double.
 #include "features.cuh"
+#include "mlp.cuh"
 
 namespace rtk {
 
@@ -158,12 +159,11 @@ __device__ __forceinline__ T block_sum(T v, T *red)
 
 // pass 3, CTA of 256 threads per image (thread = histogram bin): moments,
 // entropy and percentiles from the histogram; the partial edge blocks; the
-// 24 features
-__global__ void __launch_bounds__(256) feat_final_kernel(FeatBatch fb, float *out)
+// 24 features into f
+__device__ __forceinline__ void feat_final_image(const FeatImage &d, float *f)
 {
     __shared__ double redd[8];
     __shared__ uint32_t cum[256];
-    const FeatImage &d = fb.img[blockIdx.x];
     const int v = threadIdx.x;
     const double N = (double)d.H * d.W;
     const uint32_t h = d.hist[v];
@@ -186,7 +186,6 @@ __global__ void __launch_bounds__(256) feat_final_kernel(FeatBatch fb, float *ou
         cum[v] += add;
         __syncthreads();
     }
-    float *f = out + (int64_t)blockIdx.x * kNumFeatures;
     const int pct[9] = {1, 5, 10, 25, 50, 75, 90, 95, 99};
     for (int k = 0; k < 9; ++k) {
         const double need = pct[k] / 100.0 * N;
@@ -232,6 +231,34 @@ __global__ void __launch_bounds__(256) feat_final_kernel(FeatBatch fb, float *ou
     f[23] = (float)log1p((double)d.acc[3]);
 }
 
+__global__ void __launch_bounds__(256) feat_final_kernel(FeatBatch fb, float *out)
+{
+    feat_final_image(fb.img[blockIdx.x], out + (int64_t)blockIdx.x * kNumFeatures);
+}
+
+// pass 3 and the picker's network on the image's features, in one CTA per
+// image: warp 0 runs the same per-sample network (same order of operations,
+// same bits) as the network's forward for a chunk of tiles
+__global__ void __launch_bounds__(256) feat_final_pick_kernel(FeatBatch fb, float *out, const uint16_t *wb,
+                                                              const float *norm, int32_t *pick, float min_prob,
+                                                              int fallback)
+{
+    __shared__ float P[kMlpParams];
+    __shared__ float xn[kMlpIn];
+    __shared__ float h[2][kMlpH];
+    float *f = out + (int64_t)blockIdx.x * kNumFeatures;
+    feat_final_image(fb.img[blockIdx.x], f);
+    mlp_stage_params(wb, P);
+    __syncthreads();   // the features (written by several threads) and P
+    if (threadIdx.x < kMlpIn) xn[threadIdx.x] = (f[threadIdx.x] - norm[threadIdx.x]) / norm[kMlpIn + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    mlp_warp_hidden(P, xn, h, threadIdx.x);
+    if (threadIdx.x != 0) return;
+    float z[kMlpOut];
+    pick[blockIdx.x] = mlp_logits_pick(P, h[1], z, min_prob, fallback);
+}
+
 size_t feat_workspace_bytes(int H, int W)
 {
     const size_t nb = (size_t)((H + 7) / 8) * ((W + 7) / 8);
@@ -259,6 +286,31 @@ cudaError_t launch_features(const FeatBatch &fb, float *out, cudaStream_t s)
     feat_count_kernel<<<dim3((unsigned)gx, (unsigned)fb.n), 256, 0, s>>>(fb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     feat_final_kernel<<<(unsigned)fb.n, 256, 0, s>>>(fb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features_pick(const FeatBatch &fb, float *out, const uint16_t *wb, const float *norm,
+                                 int32_t *pick, float min_prob, int fallback, cudaStream_t s)
+{
+    int maxH = 1, maxW = 1, maxnb = 1;
+    for (int i = 0; i < fb.n; ++i) {
+        const FeatImage &d = fb.img[i];
+        maxH = d.H > maxH ? d.H : maxH;
+        maxW = d.W > maxW ? d.W : maxW;
+        const int nb = ((d.H + 7) / 8) * ((d.W + 7) / 8);
+        maxnb = nb > maxnb ? nb : maxnb;
+    }
+    feat_zero_kernel<<<(unsigned)fb.n, 256, 0, s>>>(fb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    feat_block_kernel<<<dim3((unsigned)ceil_div(maxW, kFeatSpan), (unsigned)ceil_div(maxH, 64), (unsigned)fb.n), 256, 0,
+                        s>>>(fb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int gx = (int)ceil_div(maxnb, 256);
+    if (gx > 512) gx = 512;
+    feat_count_kernel<<<dim3((unsigned)gx, (unsigned)fb.n), 256, 0, s>>>(fb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    feat_final_pick_kernel<<<(unsigned)fb.n, 256, 0, s>>>(fb, out, wb, norm, pick, min_prob, fallback);
     return cudaGetLastError();
 }
 

@@ -26,5 +26,9 @@ struct FeatBatch {
 size_t feat_workspace_bytes(int H, int W);
 // out: n x kNumFeatures float32, row-major
 cudaError_t launch_features(const FeatBatch &fb, float *out, cudaStream_t s);
+// the features, then the picker network on each image's features in the same
+// launch as their last pass (picks as the network's forward gives them)
+cudaError_t launch_features_pick(const FeatBatch &fb, float *out, const uint16_t *wb, const float *norm,
+                                 int32_t *pick, float min_prob, int fallback, cudaStream_t s);
 
 }  // namespace rtk

@@ -191,30 +191,13 @@ __global__ void __launch_bounds__(kFwdWarps * 32) mlp_forward_warp_kernel(const 
     __shared__ float P[kMlpParams];
     __shared__ float h[kFwdWarps][2][kMlpH];
     __shared__ float xn[kFwdWarps][kMlpIn];
-    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) P[i] = bf(wb[i]);
+    mlp_stage_params(wb, P);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * kFwdWarps + w;
     if (b < B && lane < kMlpIn) xn[w][lane] = (x[(int64_t)b * kMlpIn + lane] - norm[lane]) / norm[kMlpIn + lane];
     __syncthreads();
     if (b >= B) return;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int j = lane + 32 * q;
-        float s = P[kB1 + j];
-#pragma unroll
-        for (int i = 0; i < kMlpIn; ++i) s = fmaf(P[kW1 + j * kMlpIn + i], xn[w][i], s);
-        h[w][0][j] = fmaxf(s, 0.f);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int j = lane + 32 * q;
-        float s = P[kB2 + j];
-#pragma unroll 8
-        for (int i = 0; i < kMlpH; ++i) s = fmaf(P[kW2 + j * kMlpH + i], h[w][0][i], s);
-        h[w][1][j] = fmaxf(s, 0.f);
-    }
-    __syncwarp();
+    mlp_warp_hidden(P, xn[w], h[w], lane);
     if (act) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -224,23 +207,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32) mlp_forward_warp_kernel(const 
     }
     if (lane != 0) return;
     float z[kMlpOut];
+    const int best = mlp_logits_pick(P, h[w][1], z, min_prob, fallback);
+    if (logits) {
 #pragma unroll
-    for (int k = 0; k < kMlpOut; ++k) z[k] = P[kB3 + k];
-    for (int j = 0; j < kMlpH; ++j) {
-#pragma unroll
-        for (int k = 0; k < kMlpOut; ++k) z[k] = fmaf(P[kW3 + k * kMlpH + j], h[w][1][j], z[k]);
-    }
-    int best = 0;
-#pragma unroll
-    for (int k = 0; k < kMlpOut; ++k) {
-        if (logits) logits[(int64_t)b * kMlpOut + k] = z[k];
-        if (z[k] > z[best]) best = k;
-    }
-    if (min_prob > 0.f) {
-        float se = 0.f;
-#pragma unroll
-        for (int k = 0; k < kMlpOut; ++k) se += expf(z[k] - z[best]);
-        if (1.f / se < min_prob) best = fallback;
+        for (int k = 0; k < kMlpOut; ++k) logits[(int64_t)b * kMlpOut + k] = z[k];
     }
     if (pick) pick[b] = best;
 }

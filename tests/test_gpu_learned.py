@@ -264,6 +264,33 @@ def test_learned_policy_same_bytes_as_plain(rt, classes):
         ctx.close()
 
 
+def test_chain_picks_equal_the_network_forward(rt):
+    """The chain computes its picks in the features' last launch; they equal
+    the network's forward on rt_tile_features of the same tiles (the same
+    bits), alone and in a chunk whose classes make the picks matter, with and
+    without the confidence fall-back."""
+    import os
+    from paper_1405_7958_gb300 import picker as pkmod
+    pk = pkmod.load(os.path.join(os.path.dirname(rt.__file__), "data", "picker_config4.npz"))
+    shapes = [(1024, 1280), (2048, 1536), (300, 500), (1536, 3072)]
+    imgs = [rt.synth_tile(H, W, 500 + i, 60 + 40 * i) for i, (H, W) in enumerate(shapes)]
+    feats = rt.tile_features(imgs)
+    for min_prob in (0, 600, 990):
+        want = host(pk.forward(feats, min_prob=min_prob / 1000.0, fallback=3)[2]).tolist()
+        ctx = rt.Context()
+        pk.attach(ctx)
+        params = rt.SegParams(policy=1, pick_min_prob=min_prob)
+        got = []
+        for im in imgs:
+            rt.segment_batch([im], params, ctx=ctx)
+            got += rt.last_picks(ctx)
+        assert got == want
+        rt.set_picker_classes(VARIANT_CLASSES, ctx)
+        rt.segment_batch(imgs, params, ctx=ctx)
+        assert rt.last_picks(ctx) == want
+        ctx.close()
+
+
 def _height_picker(rt):
     """A hand-set network whose class depends on the tile height alone:
     h = H / 1024, logits (0.5, h, 2h - 0.75) -> raster below H = 512, queue
